@@ -1,0 +1,171 @@
+"""One M-rPIE iteration over the grouped schedule, with optional XCORR_A +
+Adam position refinement (M-rPIE and Adam-based position refinement
+sections; Eqs. 4-9, Algorithm 1).
+
+Per group S (a set of positions with pairwise-disjoint crop boxes), with O and
+P the estimates at the start of the group:
+
+    Pint(r)  = sum_p |P_p(r)|^2,   Pmax = max_r Pint(r)
+    for j in S:
+        o        = crop of O at corner_j                           (Eq. 4)
+        psi_p    = P_p o                                            (Eq. 1)
+        Psi_p    = F psi_p                                          (Eq. 2)
+        S_j      = sum_p |Psi_p|^2
+        err     += sum_u (sqrt(S_j) - sqrt(I_j))^2
+        Psi'_p   = sqrt(I_j) Psi_p / (sqrt(S_j) + eps)              (Eq. 7, reading R1)
+        D_p      = F^-1 Psi'_p - psi_p
+        o'       = o + alpha_O sum_p D_p conj(P_p)
+                         / (gamma Pmax + (1-gamma) Pint + reg_eps Pmax)   (Eq. 6)
+        write o' back into O (disjoint boxes: no conflicts)
+        num_p   += D_p conj(o);  den += beta max|o|^2 + (1-beta)|o|^2
+        [refine] s_j = peak of xcorr(o, o'),  g_j = -s_j
+    P_p += alpha_P num_p / (den + reg_eps sum_j max|o_j|^2)         (Eq. 5, ratio of sums)
+
+Readings: both updates read the pre-update o_j and P (the right-hand sides of
+Eqs. 5-6 are unprimed).  Inside a group the probe update is the ratio of the
+summed numerators and denominators; for a group of one position it is Eq. 5
+exactly, and ``max_group=1`` gives the paper's sequential algorithm.  M-rPIE
+with beta = gamma = 1 is M-ePIE (M-rPIE section).  The reported error is
+sum (sqrt S - sqrt I)^2 over all patterns / sum I, taken before the
+constraint.  With refinement on, every position measured in the iteration gets
+one Adam step at the end of the iteration (Eqs. 8-9, Algorithm 1) and the
+positions are clamped to keep the crop inside the object; regrouping happens
+at the start of the next iteration.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .adam import adam_step
+from .grouping import greedy_groups
+from .model import F, Finv, crop_corners, from_detector
+from .registration import xcorr_peak
+
+
+@dataclass
+class RPIEParams:
+    alpha_O: float = 1.0      # object step size (Eq. 6)
+    alpha_P: float = 1.0      # probe step size (Eq. 5)
+    beta: float = 1.0         # probe regulariser (Eq. 5); 1 -> ePIE-like
+    gamma: float = 0.1        # object regulariser (Eq. 6)
+    eps: float = 1e-8         # modulus-constraint guard
+    reg_eps: float = 1e-12    # relative guard of the update denominators
+    max_group: int = 0        # 0 = unlimited, 1 = sequential paper algorithm
+    update_probe: bool = True
+
+
+@dataclass
+class RefineParams:
+    upsample: int = 20        # U
+    lr: float = 0.5           # Adam step size, pixels
+    b1: float = 0.9
+    b2: float = 0.999
+    eps: float = 1e-8
+    start_iter: int = 0       # first iteration (0-based, global) that refines
+    max_step: float = 0.0     # per-axis clamp of one Adam step, 0 = none
+
+
+@dataclass
+class State:
+    O: np.ndarray             # complex128 (Hy, Hx)
+    P: np.ndarray             # complex128 (M, W, W)
+    pos: np.ndarray           # float64 (N, 2), (y, x) top-left, object pixels
+    m: np.ndarray = None
+    v: np.ndarray = None
+    t: int = 0                # Adam steps taken
+    it: int = 0               # iterations run
+    last_shift: np.ndarray = None
+    gaps: list = field(default_factory=list)
+
+    @classmethod
+    def create(cls, O0, P0, pos0):
+        pos = np.asarray(pos0, dtype=np.float64).copy()
+        return cls(O=np.asarray(O0, dtype=np.complex128).copy(),
+                   P=np.asarray(P0, dtype=np.complex128).copy(), pos=pos,
+                   m=np.zeros_like(pos), v=np.zeros_like(pos),
+                   last_shift=np.zeros_like(pos))
+
+
+def rpie_group(O, P, I, corners, members, prm, U=0):
+    """Update O (in place) for every position of one group and P at its end.
+
+    Returns (error numerator, shifts (len(members), 2), gaps).
+    """
+    W = P.shape[-1]
+    Pint = np.sum(np.abs(P) ** 2, axis=0)
+    Pmax = Pint.max()
+    obj_den = prm.gamma * Pmax + (1.0 - prm.gamma) * Pint + prm.reg_eps * Pmax
+    num = np.zeros_like(P)
+    den = np.zeros((W, W))
+    omax_sum = 0.0
+    err = 0.0
+    shifts = np.zeros((len(members), 2))
+    gaps = []
+    for i, j in enumerate(members):
+        cy, cx = int(corners[j][0]), int(corners[j][1])
+        o = O[cy:cy + W, cx:cx + W].copy()
+        psi = P * o[None]
+        Psi = F(psi)
+        S = np.sum(np.abs(Psi) ** 2, axis=0)
+        sqI = np.sqrt(from_detector(np.asarray(I[j], dtype=np.float64)))
+        err += float(np.sum((np.sqrt(S) - sqI) ** 2))
+        Psi_c = Psi * (sqI / (np.sqrt(S) + prm.eps))[None]
+        D = Finv(Psi_c) - psi
+        o_new = o + prm.alpha_O * np.sum(D * np.conj(P), axis=0) / obj_den
+        O[cy:cy + W, cx:cx + W] = o_new
+        a2 = np.abs(o) ** 2
+        om = float(a2.max())
+        num += D * np.conj(o)[None]
+        den += prm.beta * om + (1.0 - prm.beta) * a2
+        omax_sum += om
+        if U:
+            shifts[i], gap = xcorr_peak(o, o_new, U)
+            gaps.append(gap)
+    if prm.update_probe:
+        P += prm.alpha_P * num / (den + prm.reg_eps * omax_sum)[None]
+    return err, shifts, gaps
+
+
+def clamp_positions(pos, W, Hy, Hx):
+    """Keep every crop box inside the object: 0 <= y <= Hy-W, 0 <= x <= Hx-W."""
+    out = pos.copy()
+    out[:, 0] = np.clip(out[:, 0], 0.0, Hy - W)
+    out[:, 1] = np.clip(out[:, 1], 0.0, Hx - W)
+    return out
+
+
+def iterate(state, I, prm, rfn=None, order=None, groups=None):
+    """Run one iteration in place on ``state``; returns the normalised error.
+
+    ``groups`` (optional) overrides the greedy partition, for tests.
+    """
+    W = state.P.shape[-1]
+    refine_on = rfn is not None and state.it >= rfn.start_iter
+    U = rfn.upsample if refine_on else 0
+    if groups is None:
+        groups = greedy_groups(state.pos, W, order, prm.max_group)
+    corners = crop_corners(state.pos)
+    err = 0.0
+    g_meas = np.zeros_like(state.pos)
+    state.gaps = []
+    for members in groups:
+        e, sh, gaps = rpie_group(state.O, state.P, I, corners, members, prm, U)
+        err += e
+        if refine_on:
+            g_meas[members] = -sh
+            state.gaps.extend(gaps)
+    if refine_on:
+        state.t += 1
+        pos, state.m, state.v = adam_step(state.pos, state.m, state.v, g_meas,
+                                          state.t, rfn.lr, rfn.b1, rfn.b2,
+                                          rfn.eps, rfn.max_step)
+        state.pos = clamp_positions(pos, W, *state.O.shape)
+        state.last_shift = g_meas
+    state.it += 1
+    total = float(np.sum(np.asarray(I, dtype=np.float64)))
+    return err / total if total > 0 else 0.0
+
+
+def run(state, I, prm, n_iter, rfn=None, order=None):
+    """n_iter iterations; returns the list of per-iteration errors."""
+    return [iterate(state, I, prm, rfn, order) for _ in range(n_iter)]
