@@ -1,0 +1,172 @@
+/*
+ * pty.h -- C ABI of libpty, a B300 (sm_103a) implementation of mixed-state
+ * rPIE ("M-rPIE") ptychographic reconstruction with Adam-controlled XCORR_A
+ * position refinement, after Guzzi et al., "A modular software framework for
+ * the design and implementation of ptychography algorithms"
+ * (arXiv 2205.04295).
+ *
+ * Conventions shared by every call:
+ *   - Every function returns PTY_OK (0) or a PTY_E* code; on failure
+ *     pty_last_error() returns a message for the calling thread.  No C++
+ *     exception crosses this boundary.
+ *   - Complex arrays are interleaved complex64 (float re, float im), row-major.
+ *   - Object O: Hy x Hx.  Probe P: M modes of W x W ("P_p" of Eq. 4).
+ *   - Diffraction stack I: N patterns of W x W uint16 photon counts, stored
+ *     detector-centred (zero spatial frequency at pixel (W/2, W/2)).
+ *   - Positions: N pairs (y, x), float32, the top-left corner of the crop box
+ *     o_j in object pixels.  rPIE crops at floor(pos + 0.5); the
+ *     differentiable form samples bilinearly at the exact position.
+ *   - mem_kind PTY_MEM_HOST: a host pointer (pageable or pinned);
+ *     PTY_MEM_DEVICE: a device pointer on the handle's current device.
+ *   - Work is ordered on the handle's stream.  Calls that return host data
+ *     synchronise that stream; all others may return before the GPU is done.
+ *   - Pattern sizes supported by the kernels: W in {32, 64, 96, 128, 192, 256}.
+ *   - A handle is not thread-safe: one thread at a time per handle.
+ */
+#ifndef PTY_H_
+#define PTY_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTY_ABI_VERSION 1
+
+enum {
+  PTY_OK = 0,
+  PTY_EINVAL = 1,   /* bad argument: null pointer, size, unsupported W, ... */
+  PTY_ENOMEM = 2,   /* device allocation (or the caller's allocator) failed */
+  PTY_ECUDA = 3,    /* a CUDA runtime call failed */
+  PTY_EDATA = 4,    /* data outside the model: crop outside O, non-finite values */
+  PTY_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+  PTY_ESTATE = 6    /* call out of order, e.g. iterations before pty_set_data */
+};
+
+enum { PTY_MEM_HOST = 0, PTY_MEM_DEVICE = 1 };
+
+typedef struct pty_handle pty_handle;
+
+/* Optional device allocator: return a device pointer of at least `bytes`
+ * bytes usable on `stream`, or NULL on failure.  `free` releases it. */
+typedef void* (*pty_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pty_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+  int W;                /* pattern side length (pixels) */
+  int M;                /* number of probe modes, >= 1 */
+  int N;                /* number of scan positions, >= 1 */
+  int Hy, Hx;           /* object size, >= W */
+  void* stream;         /* cudaStream_t; NULL = the legacy default stream */
+  pty_alloc_fn alloc;   /* NULL = cudaMalloc / cudaFree */
+  pty_free_fn free;
+  void* alloc_ctx;
+  size_t scratch_bytes; /* cap on the far-field scratch; 0 = 64 MiB.  The
+                           scratch holds M far-field waves per patch of a chunk
+                           of one group; a smaller cap means smaller chunks. */
+  int flags;            /* reserved, 0 */
+} pty_problem_desc;
+
+/* Update parameters of M-rPIE (M-rPIE section, Eqs. 5-7). */
+typedef struct {
+  float alpha_O;   /* object step size alpha_O (Eq. 6) */
+  float alpha_P;   /* probe step size alpha_P (Eq. 5) */
+  float beta;      /* probe regulariser beta (Eq. 5); beta = gamma = 1 is M-ePIE */
+  float gamma;     /* object regulariser gamma (Eq. 6) */
+  float eps;       /* modulus-constraint guard: f = sqrt(I)/(sqrt(S)+eps), in
+                      amplitude units (sqrt photons); 1 regularises pixels whose
+                      model is darker than one photon */
+  float reg_eps;   /* relative guard added to both update denominators; where
+                      a denominator is exactly 0 the update is skipped */
+  int max_group;   /* positions per disjoint group: 0 = unlimited, 1 = the
+                      paper's sequential order */
+  int update_probe;/* 0 = hold the probe fixed */
+} pty_rpie_params;
+
+/* Position refinement (Adam-based position refinement section,
+ * Eqs. 8-9, Algorithm 1). */
+typedef struct {
+  int upsample;    /* U: registration resolution 1/U pixel; K = ceil(1.5 U) */
+  float lr;        /* Adam step size (pixels) */
+  float b1, b2;    /* Adam moment decays */
+  float eps;       /* Adam denominator guard */
+  int start_iter;  /* first iteration (counted over the handle's life) that refines */
+  float max_step;  /* per-axis clamp of one step; 0 = none */
+} pty_refine_params;
+
+/* Message describing the last failure on this thread ("" if none). */
+const char* pty_last_error(void);
+int pty_abi_version(void);
+
+/* Create a problem; allocates all device state on the current device.
+ * Ownership: the handle owns its device memory until pty_destroy. */
+int pty_init_problem(const pty_problem_desc* d, pty_handle** out);
+int pty_destroy(pty_handle* h);
+
+/* Copy in the data and the initial guesses (stream-ordered; the caller keeps
+ * its buffers).  I: N*W*W uint16, pos: N*2 float, O0: Hy*Hx complex64,
+ * P0: M*W*W complex64, all of the same mem_kind.  Fails with PTY_EDATA if a
+ * crop box leaves the object or a value is not finite.  Resets the Adam
+ * state and the iteration counter. */
+int pty_set_data(pty_handle* h, const uint16_t* I, const float* pos,
+                 const void* O0, const void* P0, int mem_kind);
+
+/* Optional scan order used by the greedy grouping: a permutation of 0..N-1
+ * (host memory), or NULL for index order.  (The random draw, if any, is the
+ * caller's.) */
+int pty_set_scan_order(pty_handle* h, const int32_t* order);
+
+/* n_iter M-rPIE iterations (Eqs. 4-7) over the disjoint-group schedule.
+ * err_out (host, may be NULL) receives n_iter normalised errors
+ * sum (sqrt S - sqrt I)^2 / sum I; requesting them synchronises. */
+int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p,
+                       float* err_out);
+
+/* Run only groups [g_begin, g_end) of the current grouping, without touching
+ * positions or the iteration counter (for sampled checks of one full-size
+ * launch sequence).  err_out (host, may be NULL): one value, the error
+ * numerator over those groups divided by sum I. */
+int pty_run_groups(pty_handle* h, int g_begin, int g_end,
+                   const pty_rpie_params* p, float* err_out);
+
+/* Current grouping (computed from the current positions): *n_groups, and if
+ * non-NULL group_ptr (n_groups+1) and group_pos (N), host memory. */
+int pty_get_groups(pty_handle* h, int* n_groups, int32_t* group_ptr,
+                   int32_t* group_pos);
+
+/* Copies out / in.  Sizes as in pty_set_data; Adam state m, v: N*2 float. */
+int pty_get_object(pty_handle* h, void* dst, int mem_kind);
+int pty_set_object(pty_handle* h, const void* src, int mem_kind);
+int pty_get_probe(pty_handle* h, void* dst, int mem_kind);
+int pty_set_probe(pty_handle* h, const void* src, int mem_kind);
+int pty_get_positions(pty_handle* h, float* dst, int mem_kind);
+int pty_set_positions(pty_handle* h, const float* src, int mem_kind);
+int pty_get_adam_state(pty_handle* h, float* m, float* v, int* t, int* iter,
+                       int mem_kind);
+int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t,
+                       int iter, int mem_kind);
+
+/* Model intensities sum_p |F{P_p o_j}|^2 (Eq. 4) for all j at the current
+ * O, P and rounded positions: N*W*W float, detector-centred. */
+int pty_model_intensities(pty_handle* h, float* dst, int mem_kind);
+
+/* Host-only greedy grouping (no GPU needed): positions pos (N*2, host),
+ * boxes of side W, optional order (NULL = index order), max_group (0 =
+ * unlimited).  Writes group_ptr (capacity N+1), group_pos (N), *n_groups.
+ * Each position goes to the first group with no overlapping box. */
+int pty_group_positions(const float* pos, int N, int W, int max_group,
+                        const int32_t* order, int32_t* group_ptr,
+                        int32_t* group_pos, int* n_groups);
+
+/* Unnormalised 2-D DFT of `batch` W x W complex64 arrays, in place, device
+ * memory, through the same line FFTs the reconstruction uses (a check of
+ * the FFT alone).  inverse = 0: exp(-2 pi i ...), 1: exp(+2 pi i ...). */
+int pty_fft2(void* data, int W, int batch, int inverse, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTY_H_ */

@@ -21,7 +21,13 @@ P the estimates at the start of the group:
         [refine] s_j = peak of xcorr(o, o'),  g_j = -s_j
     P_p += alpha_P num_p / (den + reg_eps sum_j max|o_j|^2)         (Eq. 5, ratio of sums)
 
-Readings: both updates read the pre-update o_j and P (the right-hand sides of
+Readings: eps is taken at the one-photon amplitude level (eps = 1 by
+default): with eps -> 0 the constrained wave at a detector pixel where the
+model is (numerically) dark but photons were counted has full amplitude and
+the phase of rounding noise, so the iteration stops being a continuous
+function of its inputs.  Where an update denominator is exactly zero its
+numerator is zero as well and the update there is skipped.  Both updates
+read the pre-update o_j and P (the right-hand sides of
 Eqs. 5-6 are unprimed).  Inside a group the probe update is the ratio of the
 summed numerators and denominators; for a group of one position it is Eq. 5
 exactly, and ``max_group=1`` gives the paper's sequential algorithm.  M-rPIE
@@ -48,7 +54,7 @@ class RPIEParams:
     alpha_P: float = 1.0      # probe step size (Eq. 5)
     beta: float = 1.0         # probe regulariser (Eq. 5); 1 -> ePIE-like
     gamma: float = 0.1        # object regulariser (Eq. 6)
-    eps: float = 1e-8         # modulus-constraint guard
+    eps: float = 1.0          # modulus-constraint guard, amplitude units (sqrt photons)
     reg_eps: float = 1e-12    # relative guard of the update denominators
     max_group: int = 0        # 0 = unlimited, 1 = sequential paper algorithm
     update_probe: bool = True
@@ -111,7 +117,8 @@ def rpie_group(O, P, I, corners, members, prm, U=0):
         err += float(np.sum((np.sqrt(S) - sqI) ** 2))
         Psi_c = Psi * (sqI / (np.sqrt(S) + prm.eps))[None]
         D = Finv(Psi_c) - psi
-        o_new = o + prm.alpha_O * np.sum(D * np.conj(P), axis=0) / obj_den
+        upd = np.sum(D * np.conj(P), axis=0)
+        o_new = o + prm.alpha_O * np.divide(upd, obj_den, out=np.zeros_like(upd), where=obj_den > 0)
         O[cy:cy + W, cx:cx + W] = o_new
         a2 = np.abs(o) ** 2
         om = float(a2.max())
@@ -122,7 +129,8 @@ def rpie_group(O, P, I, corners, members, prm, U=0):
             shifts[i], gap = xcorr_peak(o, o_new, U)
             gaps.append(gap)
     if prm.update_probe:
-        P += prm.alpha_P * num / (den + prm.reg_eps * omax_sum)[None]
+        pden = np.broadcast_to(den + prm.reg_eps * omax_sum, num.shape)
+        P += prm.alpha_P * np.divide(num, pden, out=np.zeros_like(num), where=pden > 0)
     return err, shifts, gaps
 
 

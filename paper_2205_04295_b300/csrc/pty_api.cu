@@ -1,0 +1,650 @@
+// Host side of libpty: the C ABI declared in include/pty.h.
+//
+// The handle owns every device array of one reconstruction problem.  One
+// M-rPIE iteration (M-rPIE section of Guzzi et al., arXiv 2205.04295) is run
+// as: round the positions to crop corners, partition them into groups of
+// pairwise-disjoint boxes (greedy first fit), and for each group, for each
+// chunk of at most Qc patches, launch the three passes (rows_fwd, cols,
+// rows_inv), then apply the group's probe update.  Qc is set so that the
+// chunk's far-field waves (Qc * M * W^2 complex64) fit the scratch budget and
+// stay resident in L2.
+#include "pty_internal.h"
+#include "../../include/pty.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      return fail(PTY_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                        \
+  } while (0)
+
+#define TRY(call)              \
+  do {                         \
+    int r_ = (call);           \
+    if (r_ != PTY_OK) return r_; \
+  } while (0)
+
+__global__ void k_sum_u16(const uint16_t* __restrict__ I, size_t n,
+                          unsigned long long* out) {
+  unsigned long long s = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    s += I[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);  // integer: exact in any order
+}
+
+__global__ void k_iota(int* p, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = i;
+}
+
+// Greedy first-fit grouping.  Boxes with corners a, b overlap iff
+// |a.y - b.y| < W and |a.x - b.x| < W; only the 3x3 neighbouring cells of a
+// W-sized grid can hold an overlapping corner.
+void greedy_group(const std::vector<int2>& c, int W, const int32_t* order,
+                  int max_group, std::vector<int>& gptr, std::vector<int>& gpos) {
+  const int N = (int)c.size();
+  int miny = 0, minx = 0, maxy = 0, maxx = 0;
+  for (int j = 0; j < N; ++j) {
+    if (j == 0 || c[j].x < miny) miny = c[j].x;
+    if (j == 0 || c[j].y < minx) minx = c[j].y;
+    if (j == 0 || c[j].x > maxy) maxy = c[j].x;
+    if (j == 0 || c[j].y > maxx) maxx = c[j].y;
+  }
+  const int ncy = (maxy - miny) / W + 1, ncx = (maxx - minx) / W + 1;
+  std::vector<std::vector<int>> cells((size_t)ncy * ncx);
+  std::vector<int> group_of(N, -1), gsize, stamp;
+  std::vector<std::vector<int>> members;
+  for (int n = 0; n < N; ++n) {
+    const int j = order ? order[n] : n;
+    const int cy = (c[j].x - miny) / W, cx = (c[j].y - minx) / W;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int yy = cy + dy, xx = cx + dx;
+        if (yy < 0 || xx < 0 || yy >= ncy || xx >= ncx) continue;
+        for (int i : cells[(size_t)yy * ncx + xx])
+          if (std::abs(c[i].x - c[j].x) < W && std::abs(c[i].y - c[j].y) < W)
+            stamp[group_of[i]] = n;
+      }
+    int g = 0;
+    const int G = (int)members.size();
+    while (g < G && (stamp[g] == n || (max_group > 0 && gsize[g] >= max_group))) ++g;
+    if (g == G) {
+      members.emplace_back();
+      gsize.push_back(0);
+      stamp.push_back(-1);
+    }
+    members[g].push_back(j);
+    ++gsize[g];
+    group_of[j] = g;
+    cells[(size_t)cy * ncx + cx].push_back(j);
+  }
+  gptr.assign(members.size() + 1, 0);
+  gpos.clear();
+  gpos.reserve(N);
+  for (size_t g = 0; g < members.size(); ++g) {
+    gpos.insert(gpos.end(), members[g].begin(), members[g].end());
+    gptr[g + 1] = (int)gpos.size();
+  }
+}
+
+bool valid_perm(const int32_t* order, int N) {
+  std::vector<char> seen(N, 0);
+  for (int i = 0; i < N; ++i) {
+    if (order[i] < 0 || order[i] >= N || seen[order[i]]) return false;
+    seen[order[i]] = 1;
+  }
+  return true;
+}
+
+}  // namespace
+
+struct pty_handle {
+  int W = 0, M = 0, N = 0, Hy = 0, Hx = 0;
+  cudaStream_t stream = nullptr;
+  pty_alloc_fn af = nullptr;
+  pty_free_fn ff = nullptr;
+  void* actx = nullptr;
+  int device = 0;
+  pty::Tiling tl{};
+  int Qc = 1, nslots = 1;
+  float inv_w = 1.f;
+  // device state
+  float2 *O = nullptr, *P = nullptr, *tw = nullptr, *scratch = nullptr, *pnum = nullptr;
+  uint16_t* I = nullptr;
+  float *pos = nullptr, *am = nullptr, *av = nullptr, *pden = nullptr, *osum = nullptr;
+  float *omax_part = nullptr, *err_part = nullptr, *pmax_part = nullptr, *err_iter = nullptr;
+  float* shift = nullptr;
+  int2* corners = nullptr;
+  int *gpos_d = nullptr, *iota = nullptr, *flag = nullptr;
+  unsigned long long* sum_d = nullptr;
+  size_t err_part_n = 0;
+  int err_iter_cap = 0;
+  // host state
+  double sumI = 0.0;
+  bool has_data = false;
+  int adam_t = 0, iter = 0;
+  std::vector<float> pos_h;
+  std::vector<int2> corners_h;
+  std::vector<int> gptr, gpos;
+  std::vector<int32_t> order;
+  bool groups_valid = false;
+  int grouped_max = -1;
+  std::vector<void*> allocs;
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (af) {
+      p = af(bytes, stream, actx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) allocs.push_back(p);
+    return p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    auto it = std::find(allocs.begin(), allocs.end(), p);
+    if (it != allocs.end()) allocs.erase(it);
+    if (ff) ff(p, stream, actx);
+    else cudaFree(p);
+  }
+  ~pty_handle() {
+    if (stream) cudaStreamSynchronize(stream);
+    else cudaDeviceSynchronize();
+    for (void* p : allocs) {
+      if (ff) ff(p, stream, actx);
+      else cudaFree(p);
+    }
+  }
+};
+
+namespace {
+
+template <class T>
+int alloc_into(pty_handle* h, T*& p, size_t count) {
+  p = static_cast<T*>(h->dalloc(count * sizeof(T)));
+  if (!p) return fail(PTY_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+  return PTY_OK;
+}
+
+cudaMemcpyKind kind_in(int mem_kind) {
+  return mem_kind == PTY_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+}
+cudaMemcpyKind kind_out(int mem_kind) {
+  return mem_kind == PTY_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+}
+
+int check_mem_kind(int mk) {
+  if (mk != PTY_MEM_HOST && mk != PTY_MEM_DEVICE) return fail(PTY_EINVAL, "bad mem_kind %d", mk);
+  return PTY_OK;
+}
+
+int check_params(const pty_rpie_params* p) {
+  if (!p) return fail(PTY_EINVAL, "null rpie params");
+  const float v[6] = {p->alpha_O, p->alpha_P, p->beta, p->gamma, p->eps, p->reg_eps};
+  for (float x : v)
+    if (!std::isfinite(x)) return fail(PTY_EINVAL, "non-finite rpie parameter");
+  if (p->max_group < 0) return fail(PTY_EINVAL, "max_group < 0");
+  return PTY_OK;
+}
+
+// Round host positions, check the boxes, rebuild groups if needed.
+int regroup(pty_handle* h, int max_group) {
+  if (h->groups_valid && h->grouped_max == max_group) return PTY_OK;
+  const int N = h->N, W = h->W;
+  h->corners_h.resize(N);
+  for (int j = 0; j < N; ++j) {
+    const double y = h->pos_h[2 * j], x = h->pos_h[2 * j + 1];
+    if (!std::isfinite(y) || !std::isfinite(x))
+      return fail(PTY_EDATA, "position %d is not finite", j);
+    const int cy = (int)std::floor(y + 0.5), cx = (int)std::floor(x + 0.5);
+    if (cy < 0 || cx < 0 || cy + W > h->Hy || cx + W > h->Hx)
+      return fail(PTY_EDATA, "crop box of position %d (corner %d,%d) leaves the %dx%d object",
+                  j, cy, cx, h->Hy, h->Hx);
+    h->corners_h[j] = make_int2(cy, cx);
+  }
+  greedy_group(h->corners_h, W, h->order.empty() ? nullptr : h->order.data(), max_group,
+               h->gptr, h->gpos);
+  CU(cudaMemcpyAsync(h->corners, h->corners_h.data(), sizeof(int2) * N,
+                     cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->gpos_d, h->gpos.data(), sizeof(int) * N, cudaMemcpyHostToDevice,
+                     h->stream));
+  h->groups_valid = true;
+  h->grouped_max = max_group;
+  return PTY_OK;
+}
+
+pty::UpdArgs upd_args(const pty_rpie_params* p) {
+  return pty::UpdArgs{p->alpha_O, p->alpha_P, p->beta, p->gamma, p->eps, p->reg_eps};
+}
+
+int run_group(pty_handle* h, int g, const pty_rpie_params* p) {
+  const int n = h->gptr[g + 1] - h->gptr[g];
+  const int* ids = h->gpos_d + h->gptr[g];
+  const pty::UpdArgs a = upd_args(p);
+  for (int c0 = 0; c0 < n; c0 += h->Qc) {
+    const int nc = std::min(h->Qc, n - c0);
+    const int* idc = ids + c0;
+    CU(pty::launch_rows_fwd(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, h->scratch,
+                            h->omax_part, h->stream));
+    CU(pty::launch_cols(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps, h->err_part,
+                        h->stream));
+    CU(pty::launch_rows_inv(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
+                            h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
+                            c0 > 0, h->stream));
+  }
+  if (p->update_probe) {
+    const int used = (std::min(h->Qc, n) + h->tl.ppc - 1) / h->tl.ppc;
+    CU(pty::launch_probe_apply(h->tl, h->P, h->pnum, h->pden, h->osum, used, p->alpha_P,
+                               p->reg_eps, h->pmax_part, h->stream));
+  }
+  return PTY_OK;
+}
+
+int ensure_err_cap(pty_handle* h, int n) {
+  if (n <= h->err_iter_cap) return PTY_OK;
+  if (h->err_iter) {
+    CU(cudaStreamSynchronize(h->stream));
+    h->dfree(h->err_iter);
+  }
+  h->err_iter = nullptr;
+  h->err_iter_cap = 0;
+  TRY(alloc_into(h, h->err_iter, (size_t)std::max(n, 64)));
+  h->err_iter_cap = std::max(n, 64);
+  return PTY_OK;
+}
+
+int check_handle(pty_handle* h, bool need_data) {
+  if (!h) return fail(PTY_EINVAL, "null handle");
+  if (need_data && !h->has_data) return fail(PTY_ESTATE, "pty_set_data has not been called");
+  CU(cudaSetDevice(h->device));
+  return PTY_OK;
+}
+
+int finite_check(pty_handle* h, const void* dev, size_t nfloat, const char* what) {
+  CU(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  CU(pty::launch_finite_check(static_cast<const float*>(dev), nfloat, h->flag, h->stream));
+  int f = 0;
+  CU(cudaMemcpyAsync(&f, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (f) return fail(PTY_EDATA, "%s holds a non-finite value", what);
+  return PTY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pty_last_error(void) { return g_err.c_str(); }
+int pty_abi_version(void) { return PTY_ABI_VERSION; }
+
+int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
+  g_err.clear();
+  if (!d || !out) return fail(PTY_EINVAL, "null argument");
+  *out = nullptr;
+  if (!pty::supported_W(d->W)) return fail(PTY_EINVAL, "unsupported pattern size W=%d", d->W);
+  if (d->M < 1 || d->M > 16) return fail(PTY_EINVAL, "M=%d outside 1..16", d->M);
+  if (d->N < 1) return fail(PTY_EINVAL, "N=%d < 1", d->N);
+  if (d->Hy < d->W || d->Hx < d->W) return fail(PTY_EINVAL, "object %dx%d smaller than W", d->Hy, d->Hx);
+  if ((d->alloc == nullptr) != (d->free == nullptr))
+    return fail(PTY_EINVAL, "alloc and free must be given together");
+  pty_handle* h = new (std::nothrow) pty_handle();
+  if (!h) return fail(PTY_ENOMEM, "host allocation failed");
+  h->W = d->W; h->M = d->M; h->N = d->N; h->Hy = d->Hy; h->Hx = d->Hx;
+  h->stream = static_cast<cudaStream_t>(d->stream);
+  h->af = d->alloc; h->ff = d->free; h->actx = d->alloc_ctx;
+  auto bail = [&](int rc) { delete h; return rc; };
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(PTY_ECUDA, "no CUDA device"));
+  }
+  h->tl = pty::make_tiling(h->W, h->M);
+  if (cudaError_t e = pty::set_smem_limits(h->tl); e != cudaSuccess)
+    return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
+  const size_t W2 = (size_t)h->W * h->W;
+  const size_t budget = d->scratch_bytes ? d->scratch_bytes : ((size_t)64 << 20);
+  h->Qc = (int)std::max<size_t>(1, budget / (W2 * h->M * sizeof(float2)));
+  h->Qc = std::min(h->Qc, h->N);
+  h->nslots = (h->Qc + h->tl.ppc - 1) / h->tl.ppc;
+  h->inv_w = (float)(1.0 / h->W);
+  const int nrb = h->W / h->tl.R;
+  h->err_part_n = (size_t)h->N * (h->W / h->tl.CB);
+  int rc = PTY_OK;
+  if ((rc = alloc_into(h, h->O, (size_t)h->Hy * h->Hx)) ||
+      (rc = alloc_into(h, h->P, (size_t)h->M * W2)) ||
+      (rc = alloc_into(h, h->tw, (size_t)h->W)) ||
+      (rc = alloc_into(h, h->scratch, (size_t)h->Qc * h->M * W2)) ||
+      (rc = alloc_into(h, h->pnum, (size_t)h->nslots * h->M * W2)) ||
+      (rc = alloc_into(h, h->pden, (size_t)h->nslots * W2)) ||
+      (rc = alloc_into(h, h->osum, (size_t)h->nslots)) ||
+      (rc = alloc_into(h, h->omax_part, (size_t)h->Qc * nrb)) ||
+      (rc = alloc_into(h, h->err_part, h->err_part_n)) ||
+      (rc = alloc_into(h, h->pmax_part, (size_t)h->tl.n_pmax)) ||
+      (rc = alloc_into(h, h->I, (size_t)h->N * W2)) ||
+      (rc = alloc_into(h, h->pos, (size_t)2 * h->N)) ||
+      (rc = alloc_into(h, h->am, (size_t)2 * h->N)) ||
+      (rc = alloc_into(h, h->av, (size_t)2 * h->N)) ||
+      (rc = alloc_into(h, h->shift, (size_t)2 * h->N)) ||
+      (rc = alloc_into(h, h->corners, (size_t)h->N)) ||
+      (rc = alloc_into(h, h->gpos_d, (size_t)h->N)) ||
+      (rc = alloc_into(h, h->iota, (size_t)h->N)) ||
+      (rc = alloc_into(h, h->flag, (size_t)4)) ||
+      (rc = alloc_into(h, h->sum_d, (size_t)1)))
+    return bail(rc);
+  std::vector<float2> tw(h->W);
+  pty::make_twiddles(h->W, tw.data());
+  if (cudaMemcpyAsync(h->tw, tw.data(), sizeof(float2) * h->W, cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->err_part, 0, sizeof(float) * h->err_part_n, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(PTY_ECUDA, "initial copies failed"));
+  }
+  k_iota<<<64, 256, 0, h->stream>>>(h->iota, h->N);
+  if (cudaGetLastError() != cudaSuccess) return bail(fail(PTY_ECUDA, "iota launch failed"));
+  *out = h;
+  return PTY_OK;
+}
+
+int pty_destroy(pty_handle* h) {
+  if (!h) return PTY_OK;
+  cudaSetDevice(h->device);
+  delete h;
+  return PTY_OK;
+}
+
+int pty_set_data(pty_handle* h, const uint16_t* I, const float* pos, const void* O0,
+                 const void* P0, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (!I || !pos || !O0 || !P0) return fail(PTY_EINVAL, "null data pointer");
+  const size_t W2 = (size_t)h->W * h->W;
+  h->has_data = false;
+  h->pos_h.resize(2 * (size_t)h->N);
+  CU(cudaMemcpyAsync(h->pos_h.data(), pos, sizeof(float) * 2 * h->N,
+                     mem_kind == PTY_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->groups_valid = false;
+  TRY(regroup(h, 0));
+  CU(cudaMemcpyAsync(h->I, I, sizeof(uint16_t) * h->N * W2, kind_in(mem_kind), h->stream));
+  CU(cudaMemcpyAsync(h->pos, h->pos_h.data(), sizeof(float) * 2 * h->N, cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaMemcpyAsync(h->O, O0, sizeof(float2) * h->Hy * h->Hx, kind_in(mem_kind), h->stream));
+  CU(cudaMemcpyAsync(h->P, P0, sizeof(float2) * h->M * W2, kind_in(mem_kind), h->stream));
+  TRY(finite_check(h, h->O, (size_t)2 * h->Hy * h->Hx, "object"));
+  TRY(finite_check(h, h->P, (size_t)2 * h->M * W2, "probe"));
+  CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->stream));
+  k_sum_u16<<<296, 256, 0, h->stream>>>(h->I, (size_t)h->N * W2, h->sum_d);
+  CU(cudaGetLastError());
+  unsigned long long s = 0;
+  CU(cudaMemcpyAsync(&s, h->sum_d, sizeof s, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemsetAsync(h->am, 0, sizeof(float) * 2 * h->N, h->stream));
+  CU(cudaMemsetAsync(h->av, 0, sizeof(float) * 2 * h->N, h->stream));
+  CU(cudaMemsetAsync(h->shift, 0, sizeof(float) * 2 * h->N, h->stream));
+  CU(pty::launch_pmax(h->tl, h->P, h->pmax_part, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->sumI = (double)s;
+  h->adam_t = 0;
+  h->iter = 0;
+  h->has_data = true;
+  return PTY_OK;
+}
+
+int pty_set_scan_order(pty_handle* h, const int32_t* order) {
+  g_err.clear();
+  if (!h) return fail(PTY_EINVAL, "null handle");
+  if (!order) {
+    h->order.clear();
+  } else {
+    if (!valid_perm(order, h->N)) return fail(PTY_EINVAL, "scan order is not a permutation of 0..N-1");
+    h->order.assign(order, order + h->N);
+  }
+  h->groups_valid = false;
+  return PTY_OK;
+}
+
+int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, float* err_out) {
+  g_err.clear();
+  TRY(check_handle(h, true));
+  TRY(check_params(p));
+  if (n_iter < 0) return fail(PTY_EINVAL, "n_iter < 0");
+  if (n_iter == 0) return PTY_OK;
+  TRY(ensure_err_cap(h, n_iter));
+  const double inv = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
+  for (int it = 0; it < n_iter; ++it) {
+    TRY(regroup(h, p->max_group));
+    const int G = (int)h->gptr.size() - 1;
+    for (int g = 0; g < G; ++g) TRY(run_group(h, g, p));
+    CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter + it, h->stream));
+    ++h->iter;
+  }
+  if (err_out) {
+    CU(cudaMemcpyAsync(err_out, h->err_iter, sizeof(float) * n_iter, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return PTY_OK;
+}
+
+int pty_run_groups(pty_handle* h, int g_begin, int g_end, const pty_rpie_params* p,
+                   float* err_out) {
+  g_err.clear();
+  TRY(check_handle(h, true));
+  TRY(check_params(p));
+  TRY(regroup(h, p->max_group));
+  const int G = (int)h->gptr.size() - 1;
+  if (g_begin < 0 || g_end > G || g_begin > g_end)
+    return fail(PTY_EINVAL, "group range [%d,%d) outside [0,%d)", g_begin, g_end, G);
+  TRY(ensure_err_cap(h, 1));
+  CU(cudaMemsetAsync(h->err_part, 0, sizeof(float) * h->err_part_n, h->stream));
+  for (int g = g_begin; g < g_end; ++g) TRY(run_group(h, g, p));
+  if (err_out) {
+    const double inv = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
+    CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter, h->stream));
+    CU(cudaMemcpyAsync(err_out, h->err_iter, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return PTY_OK;
+}
+
+int pty_get_groups(pty_handle* h, int* n_groups, int32_t* group_ptr, int32_t* group_pos) {
+  g_err.clear();
+  TRY(check_handle(h, true));
+  if (!n_groups) return fail(PTY_EINVAL, "null n_groups");
+  TRY(regroup(h, h->grouped_max < 0 ? 0 : h->grouped_max));
+  *n_groups = (int)h->gptr.size() - 1;
+  if (group_ptr) std::copy(h->gptr.begin(), h->gptr.end(), group_ptr);
+  if (group_pos) std::copy(h->gpos.begin(), h->gpos.end(), group_pos);
+  return PTY_OK;
+}
+
+#define PTY_COPY_OUT(NAME, FIELD, COUNT, T)                                         \
+  int NAME(pty_handle* h, void* dst, int mem_kind) {                                \
+    g_err.clear();                                                                  \
+    TRY(check_handle(h, false));                                                    \
+    TRY(check_mem_kind(mem_kind));                                                  \
+    if (!dst) return fail(PTY_EINVAL, "null destination");                          \
+    CU(cudaMemcpyAsync(dst, h->FIELD, sizeof(T) * (COUNT), kind_out(mem_kind), h->stream)); \
+    if (mem_kind == PTY_MEM_HOST) CU(cudaStreamSynchronize(h->stream));             \
+    return PTY_OK;                                                                  \
+  }
+
+PTY_COPY_OUT(pty_get_object, O, (size_t)h->Hy * h->Hx, float2)
+PTY_COPY_OUT(pty_get_probe, P, (size_t)h->M * h->W * h->W, float2)
+
+int pty_get_positions(pty_handle* h, float* dst, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (!dst) return fail(PTY_EINVAL, "null destination");
+  CU(cudaMemcpyAsync(dst, h->pos, sizeof(float) * 2 * h->N, kind_out(mem_kind), h->stream));
+  if (mem_kind == PTY_MEM_HOST) CU(cudaStreamSynchronize(h->stream));
+  return PTY_OK;
+}
+
+int pty_set_object(pty_handle* h, const void* src, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (!src) return fail(PTY_EINVAL, "null source");
+  CU(cudaMemcpyAsync(h->O, src, sizeof(float2) * h->Hy * h->Hx, kind_in(mem_kind), h->stream));
+  return finite_check(h, h->O, (size_t)2 * h->Hy * h->Hx, "object");
+}
+
+int pty_set_probe(pty_handle* h, const void* src, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (!src) return fail(PTY_EINVAL, "null source");
+  const size_t n = (size_t)h->M * h->W * h->W;
+  CU(cudaMemcpyAsync(h->P, src, sizeof(float2) * n, kind_in(mem_kind), h->stream));
+  TRY(finite_check(h, h->P, 2 * n, "probe"));
+  CU(pty::launch_pmax(h->tl, h->P, h->pmax_part, h->stream));
+  return PTY_OK;
+}
+
+int pty_set_positions(pty_handle* h, const float* src, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (!src) return fail(PTY_EINVAL, "null source");
+  std::vector<float> old = h->pos_h;
+  h->pos_h.resize(2 * (size_t)h->N);
+  CU(cudaMemcpyAsync(h->pos_h.data(), src, sizeof(float) * 2 * h->N,
+                     mem_kind == PTY_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->groups_valid = false;
+  const int rc = regroup(h, h->grouped_max < 0 ? 0 : h->grouped_max);
+  if (rc != PTY_OK) {
+    h->pos_h = old;
+    h->groups_valid = false;
+    return rc;
+  }
+  CU(cudaMemcpyAsync(h->pos, h->pos_h.data(), sizeof(float) * 2 * h->N, cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return PTY_OK;
+}
+
+int pty_get_adam_state(pty_handle* h, float* m, float* v, int* t, int* iter, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (m) CU(cudaMemcpyAsync(m, h->am, sizeof(float) * 2 * h->N, kind_out(mem_kind), h->stream));
+  if (v) CU(cudaMemcpyAsync(v, h->av, sizeof(float) * 2 * h->N, kind_out(mem_kind), h->stream));
+  if (t) *t = h->adam_t;
+  if (iter) *iter = h->iter;
+  CU(cudaStreamSynchronize(h->stream));
+  return PTY_OK;
+}
+
+int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t, int iter,
+                       int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (t < 0 || iter < 0) return fail(PTY_EINVAL, "negative Adam step or iteration count");
+  if (m) CU(cudaMemcpyAsync(h->am, m, sizeof(float) * 2 * h->N, kind_in(mem_kind), h->stream));
+  if (v) CU(cudaMemcpyAsync(h->av, v, sizeof(float) * 2 * h->N, kind_in(mem_kind), h->stream));
+  h->adam_t = t;
+  h->iter = iter;
+  CU(cudaStreamSynchronize(h->stream));
+  return PTY_OK;
+}
+
+int pty_model_intensities(pty_handle* h, float* dst, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, true));
+  TRY(check_mem_kind(mem_kind));
+  if (!dst) return fail(PTY_EINVAL, "null destination");
+  TRY(regroup(h, h->grouped_max < 0 ? 0 : h->grouped_max));
+  const size_t W2 = (size_t)h->W * h->W;
+  float* out = dst;
+  float* tmp = nullptr;
+  if (mem_kind == PTY_MEM_HOST) {
+    TRY(alloc_into(h, tmp, (size_t)h->N * W2));
+    out = tmp;
+  }
+  int rc = PTY_OK;
+  for (int c0 = 0; c0 < h->N && rc == PTY_OK; c0 += h->Qc) {
+    const int nc = std::min(h->Qc, h->N - c0);
+    cudaError_t e = pty::launch_rows_fwd(h->tl, h->O, h->Hx, h->P, h->iota + c0, h->corners, nc,
+                                         h->tw, h->scratch, h->omax_part, h->stream);
+    if (e == cudaSuccess)
+      e = pty::launch_cols_intensity(h->tl, h->scratch, h->iota + c0, nc, h->tw, h->inv_w, out,
+                                     h->stream);
+    if (e != cudaSuccess) rc = fail(PTY_ECUDA, "model intensity launch: %s", cudaGetErrorString(e));
+  }
+  if (rc == PTY_OK && tmp) {
+    if (cudaMemcpyAsync(dst, tmp, sizeof(float) * h->N * W2, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      rc = fail(PTY_ECUDA, "model intensity copy failed");
+  }
+  if (tmp) {
+    cudaStreamSynchronize(h->stream);
+    h->dfree(tmp);
+  }
+  return rc;
+}
+
+int pty_group_positions(const float* pos, int N, int W, int max_group, const int32_t* order,
+                        int32_t* group_ptr, int32_t* group_pos, int* n_groups) {
+  g_err.clear();
+  if (!pos || !group_ptr || !group_pos || !n_groups) return fail(PTY_EINVAL, "null argument");
+  if (N < 1 || W < 1 || max_group < 0) return fail(PTY_EINVAL, "bad size");
+  if (order && !valid_perm(order, N)) return fail(PTY_EINVAL, "order is not a permutation");
+  std::vector<int2> c(N);
+  for (int j = 0; j < N; ++j) {
+    const double y = pos[2 * j], x = pos[2 * j + 1];
+    if (!std::isfinite(y) || !std::isfinite(x)) return fail(PTY_EDATA, "position %d not finite", j);
+    c[j] = make_int2((int)std::floor(y + 0.5), (int)std::floor(x + 0.5));
+  }
+  std::vector<int> gptr, gpos;
+  greedy_group(c, W, order, max_group, gptr, gpos);
+  *n_groups = (int)gptr.size() - 1;
+  std::copy(gptr.begin(), gptr.end(), group_ptr);
+  std::copy(gpos.begin(), gpos.end(), group_pos);
+  return PTY_OK;
+}
+
+int pty_fft2(void* data, int W, int batch, int inverse, void* stream) {
+  g_err.clear();
+  if (!data || batch < 1) return fail(PTY_EINVAL, "bad argument");
+  if (!pty::supported_W(W)) return fail(PTY_EINVAL, "unsupported W=%d", W);
+  CU(pty::launch_fft2(data, W, batch, inverse, nullptr, static_cast<cudaStream_t>(stream)));
+  return PTY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Internal declarations shared by the host API (pty_api.cu) and the kernel
+// launchers (pty_rpie.cu, pty_refine.cu, pty_grad.cu).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pty {
+
+struct UpdArgs {
+  float alpha_O, alpha_P, beta, gamma, eps, reg_eps;
+};
+
+// Launch geometry of the three passes for one (W, M).
+struct Tiling {
+  int W, M;
+  int R;         // rows per CTA, row passes
+  int ppc;       // patches per CTA, row passes
+  int CB;        // columns per CTA, column pass
+  int thrA, thrB, thrC;
+  size_t smA, smB, smC, smI;  // dynamic shared memory (bytes)
+  int n_pmax;    // CTAs of the probe-apply kernel (= partial maxima)
+};
+
+bool supported_W(int W);
+Tiling make_tiling(int W, int M);
+cudaError_t set_smem_limits(const Tiling& t);
+
+// Twiddle table w_W^m = exp(-2 pi i m / W), m = 0..W-1 (host, double -> float).
+void make_twiddles(int W, float2* out);
+
+// ---- the three passes of one chunk of a group -----------------------------
+cudaError_t launch_rows_fwd(const Tiling& t, const float2* O, int Hx,
+                            const float2* P, const int* ids, const int2* corners,
+                            int npatch, const float2* tw, float2* scratch,
+                            float* omax_part, cudaStream_t s);
+cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
+                        const int* ids, int npatch, const float2* tw, float inv_w,
+                        float eps, float* err_part, cudaStream_t s);
+cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
+                            const int* ids, const int2* corners, int npatch,
+                            const float2* scratch, const float* omax_part,
+                            const float* pmax_part, const float2* tw,
+                            const UpdArgs& a, float2* pnum, float* pden,
+                            float* osum, int accumulate, cudaStream_t s);
+cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
+                               const float* pden, const float* osum, int nslots,
+                               float alpha_P, float reg_eps, float* pmax_part,
+                               cudaStream_t s);
+cudaError_t launch_pmax(const Tiling& t, const float2* P, float* pmax_part,
+                        cudaStream_t s);
+cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
+                              float* out, cudaStream_t s);
+cudaError_t launch_cols_intensity(const Tiling& t, const float2* scratch,
+                                  const int* ids, int npatch, const float2* tw,
+                                  float inv_w, float* out, cudaStream_t s);
+cudaError_t launch_fft2(void* data, int W, int batch, int inverse,
+                        const float2* tw, cudaStream_t s);
+cudaError_t launch_finite_check(const float* p, size_t n, int* flag,
+                                cudaStream_t s);
+
+}  // namespace pty

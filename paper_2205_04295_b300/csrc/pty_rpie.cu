@@ -1,0 +1,692 @@
+// M-rPIE group step on sm_103a: the three passes over one chunk of a group of
+// pairwise-disjoint crop boxes, the probe update at the end of the group, and
+// small reductions.  Equations are those of the M-rPIE section of Guzzi et
+// al. (arXiv 2205.04295): exit waves (Eq. 1, per mode as in Eq. 4), far-field
+// propagation (Eq. 2, unitary DFT), the mixed-state modulus constraint
+// (Eq. 7), the object update (Eq. 6) and the probe update (Eq. 5).
+//
+// Pass A  rows_fwd : per (row block, patches): psi_p = P_p o_j for every mode,
+//                    forward row DFTs, rows written to the far-field scratch;
+//                    also the row block's max |o_j|^2.
+// Pass B  cols     : per (column block, patch): forward column DFTs of every
+//                    mode, S = sum_p |Psi_p|^2, Psi'_p = sqrt(I)/(sqrt(S)+eps)
+//                    Psi_p, error partial sum, inverse column DFTs.
+// Pass C  rows_inv : per (row block, patches): inverse row DFTs -> psi'_p,
+//                    D_p = psi'_p - psi_p, object update written in place
+//                    (boxes of a group are disjoint), probe numerator /
+//                    denominator partial sums kept per CTA column.
+// probe_apply      : P_p += alpha_P sum(num_p) / sum(den), fixed-order sums
+//                    over the CTA-column partials; new max_r sum_p |P_p|^2.
+//
+// All reductions run in a fixed order, so results are bitwise repeatable.
+#include "pty_fft.cuh"
+#include "pty_internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace pty {
+
+namespace {
+
+PTY_D float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+PTY_D float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Block-wide reductions; every thread gets the result.  Contain barriers.
+PTY_D float block_sum(float v, float* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int i = 0; i < nw; ++i) t += red[i];  // fixed order
+  return t;
+}
+PTY_D float block_max(float v, float* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int i = 0; i < nw; ++i) t = fmaxf(t, red[i]);
+  return t;
+}
+
+// ---------------------------------------------------------------- pass A
+template <int W>
+__global__ void __launch_bounds__(256)
+k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
+           int M, int R, int ppc, const int* __restrict__ ids,
+           const int2* __restrict__ corners, int npatch,
+           const float2* __restrict__ tw_g, float2* __restrict__ scratch,
+           float* __restrict__ omax_part) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* Prow = tw + W;
+  float2* tbuf = Prow + M * R * W;
+  __shared__ float red[32];
+
+  const int r0 = blockIdx.x * R;
+  const int nrb = W / R;
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
+    const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
+    Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
+  }
+  __syncthreads();
+
+  const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
+  const bool act = line < M * R;
+  const int k = act ? line / R : 0, r = act ? line - k * R : 0;
+  float2* lbuf = tbuf + line * G::LP;
+  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  for (int lp = p0; lp < p1; ++lp) {
+    const int j = ids[lp];
+    const int2 cc = corners[j];
+    float omax = 0.f;
+    if (act && lane < G::N2) {
+      const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
+      const float2* prow = Prow + (k * R + r) * W;
+      float2 v[G::N1];
+#pragma unroll
+      for (int n1 = 0; n1 < G::N1; ++n1) {
+        const int c = G::N2 * n1 + lane;
+        const float2 o = __ldg(orow + c);
+        v[n1] = cmul(prow[c], o);
+        omax = fmaxf(omax, cabs2(o));
+      }
+      fwd_step1<W>(v, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (act && lane < G::N1) {
+      float2 z[G::N2];
+      fwd_step3<W>(z, lane, lbuf);
+      float2* dst = scratch + (((size_t)lp * M + k) * W + r0 + r) * W;
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
+    }
+    omax = block_max(omax, red);  // its barriers also guard lbuf reuse
+    if (threadIdx.x == 0) omax_part[(size_t)lp * nrb + blockIdx.x] = omax;
+  }
+}
+
+// ---------------------------------------------------------------- pass B
+template <int W>
+__global__ void __launch_bounds__(512)
+k_cols(float2* __restrict__ scratch, int M, int CB,
+       const uint16_t* __restrict__ I, const int* __restrict__ ids,
+       const float2* __restrict__ tw_g, float inv_w, float eps,
+       float* __restrict__ err_part) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* tbuf = tw + W;
+  float* Sb = reinterpret_cast<float*>(tbuf + M * CB * G::LP);
+  __shared__ float red[32];
+
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  const int lp = blockIdx.y, c0 = blockIdx.x * CB;
+  const int c = threadIdx.x % CB, rest = threadIdx.x / CB;
+  const int lane = rest % G::L, k = rest / G::L;
+  const bool act = k < M;
+  const int j = ids[lp];
+  float2* col = scratch + ((size_t)lp * M + (act ? k : 0)) * W * W + c0 + c;
+  float2* lbuf = tbuf + ((act ? k : 0) * CB + c) * G::LP;
+  __syncthreads();
+
+  float2 v[G::N1];
+  if (act && lane < G::N2) {
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = col[(size_t)(G::N2 * n1 + lane) * W];
+    fwd_step1<W>(v, lane, tw, lbuf);
+  }
+  __syncthreads();
+  float2 z[G::N2];
+  if (act && lane < G::N1) {
+    fwd_step3<W>(z, lane, lbuf);
+#pragma unroll
+    for (int k2 = 0; k2 < G::N2; ++k2)
+      Sb[(k * CB + c) * W + lane + G::N1 * k2] = cabs2(z[k2]);
+  }
+  __syncthreads();
+  float e = 0.f;
+  if (act && lane < G::N1) {
+    const int iv = (c0 + c + W / 2) % W;
+    const uint16_t* Ij = I + (size_t)j * W * W + iv;
+    const float f2 = inv_w * inv_w;
+#pragma unroll
+    for (int k2 = 0; k2 < G::N2; ++k2) {
+      const int u = lane + G::N1 * k2;
+      float s = 0.f;
+      for (int kk = 0; kk < M; ++kk) s += Sb[(kk * CB + c) * W + u];
+      const float a = sqrtf(s) * inv_w;
+      const float sI = sqrtf((float)__ldg(Ij + (size_t)((u + W / 2) % W) * W));
+      const float f = sI / (a + eps) * f2;
+      if (k == 0) {
+        const float d = a - sI;
+        e = fmaf(d, d, e);
+      }
+      z[k2] = cscale(z[k2], f);
+    }
+    inv_stepA<W>(z, lane, tw, lbuf);
+  }
+  __syncthreads();
+  if (act && lane < G::N2) {
+    inv_stepB<W>(v, lane, lbuf);
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) col[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
+  }
+  e = block_sum(e, red);
+  if (threadIdx.x == 0) err_part[(size_t)j * (W / CB) + blockIdx.x] = e;
+}
+
+// ---------------------------------------------------------------- pass C
+template <int W>
+__global__ void __launch_bounds__(256)
+k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
+           int R, int ppc, const int* __restrict__ ids,
+           const int2* __restrict__ corners, int npatch,
+           const float2* __restrict__ scratch, const float* __restrict__ omax_part,
+           const float* __restrict__ pmax_part, int n_pmax,
+           const float2* __restrict__ tw_g, UpdArgs a,
+           float2* __restrict__ pnum, float* __restrict__ pden,
+           float* __restrict__ osum, int accumulate) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  const int TB = max(M * R * G::LP, M * R * W);
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* Prow = tw + W;
+  float2* tbuf = Prow + M * R * W;  // transpose buffer, then D conj(P) terms
+  float2* num = tbuf + TB;
+  float* Pint = reinterpret_cast<float*>(num + M * R * W);
+  float* den = Pint + R * W;
+  __shared__ float s_pmax, s_omax;
+
+  const int r0 = blockIdx.x * R;
+  const int nrb = W / R;
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
+    const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
+    Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
+    num[e] = make_float2(0.f, 0.f);
+  }
+  if (threadIdx.x < 32) {
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n_pmax; i += 32) m = fmaxf(m, pmax_part[i]);
+    m = warp_max(m);
+    if (threadIdx.x == 0) s_pmax = m;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < M; ++k) s += cabs2(Prow[k * R * W + e]);
+    Pint[e] = s;
+    den[e] = 0.f;
+  }
+  const float pmax = s_pmax;
+  const float gden = a.gamma * pmax + a.reg_eps * pmax;
+
+  const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
+  const bool act = line < M * R;
+  const int k = act ? line / R : 0, r = act ? line - k * R : 0;
+  float2* lbuf = tbuf + line * G::LP;
+  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  float osum_local = 0.f;
+  for (int lp = p0; lp < p1; ++lp) {
+    const int j = ids[lp];
+    const int2 cc = corners[j];
+    if (threadIdx.x < 32) {
+      float m = 0.f;
+      for (int i = threadIdx.x; i < nrb; i += 32) m = fmaxf(m, omax_part[(size_t)lp * nrb + i]);
+      m = warp_max(m);
+      if (threadIdx.x == 0) s_omax = m;
+    }
+    if (act && lane < G::N1) {
+      const float2* src = scratch + (((size_t)lp * M + k) * W + r0 + r) * W;
+      float2 z[G::N2];
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
+      inv_stepA<W>(z, lane, tw, lbuf);
+    }
+    __syncthreads();
+    float2 v[G::N1];
+    if (act && lane < G::N2) inv_stepB<W>(v, lane, lbuf);
+    __syncthreads();  // tbuf is reused below for the D conj(P) terms
+    if (act && lane < G::N2) {
+      const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
+      float2* T = tbuf + (k * R + r) * W;
+      float2* nm = num + (k * R + r) * W;
+      const float2* prow = Prow + (k * R + r) * W;
+#pragma unroll
+      for (int n1 = 0; n1 < G::N1; ++n1) {
+        const int c = G::N2 * n1 + lane;
+        const float2 o = orow[c];
+        const float2 Pk = prow[c];
+        const float2 D = csub(v[n1], cmul(Pk, o));
+        T[c] = cmulc(D, Pk);
+        nm[c] = cadd(nm[c], cmulc(D, o));
+      }
+    }
+    __syncthreads();
+    const float om = s_omax;
+    for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+      const int rr = e / W, c = e - rr * W;
+      float2* op = O + (size_t)(cc.x + r0 + rr) * Hx + cc.y + c;
+      const float2 o = *op;
+      float2 s = make_float2(0.f, 0.f);
+      for (int kk = 0; kk < M; ++kk) s = cadd(s, tbuf[(kk * R + rr) * W + c]);
+      const float dn = fmaf(1.f - a.gamma, Pint[e], gden);
+      const float sc = dn > 0.f ? a.alpha_O / dn : 0.f;  // zero numerator too
+      *op = make_float2(fmaf(sc, s.x, o.x), fmaf(sc, s.y, o.y));
+      den[e] += fmaf(1.f - a.beta, cabs2(o), a.beta * om);
+    }
+    osum_local += om;
+    __syncthreads();
+  }
+  const int slot = blockIdx.y;
+  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
+    const int kk = e / (R * W), rem = e - kk * R * W, rr = rem / W, c = rem - rr * W;
+    const size_t g = (((size_t)slot * M + kk) * W + r0 + rr) * W + c;
+    pnum[g] = accumulate ? cadd(pnum[g], num[e]) : num[e];
+  }
+  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+    const int rr = e / W, c = e - rr * W;
+    const size_t g = ((size_t)slot * W + r0 + rr) * W + c;
+    pden[g] = accumulate ? pden[g] + den[e] : den[e];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    osum[slot] = accumulate ? osum[slot] + osum_local : osum_local;
+}
+
+// ------------------------------------------------------------- probe apply
+__global__ void __launch_bounds__(256)
+k_probe_apply(float2* __restrict__ P, int M, int WW, const float2* __restrict__ pnum,
+              const float* __restrict__ pden, const float* __restrict__ osum,
+              int nslots, float alpha_P, float reg_eps, float* __restrict__ pmax_part) {
+  __shared__ float red[32];
+  float os = 0.f;
+  for (int s = 0; s < nslots; ++s) os += osum[s];
+  const float guard = reg_eps * os;
+  float lmax = 0.f;
+  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < WW; pix += gridDim.x * blockDim.x) {
+    float d = 0.f;
+    for (int s = 0; s < nslots; ++s) d += pden[(size_t)s * WW + pix];
+    const float dd = d + guard;
+    const float sc = dd > 0.f ? alpha_P / dd : 0.f;  // zero numerator too
+    float pint = 0.f;
+    for (int k = 0; k < M; ++k) {
+      float2 n = make_float2(0.f, 0.f);
+      for (int s = 0; s < nslots; ++s) n = cadd(n, pnum[((size_t)s * M + k) * WW + pix]);
+      float2 p = P[(size_t)k * WW + pix];
+      p = make_float2(fmaf(sc, n.x, p.x), fmaf(sc, n.y, p.y));
+      P[(size_t)k * WW + pix] = p;
+      pint += cabs2(p);
+    }
+    lmax = fmaxf(lmax, pint);
+  }
+  lmax = block_max(lmax, red);
+  if (threadIdx.x == 0) pmax_part[blockIdx.x] = lmax;
+}
+
+__global__ void __launch_bounds__(256)
+k_pmax(const float2* __restrict__ P, int M, int WW, float* __restrict__ pmax_part) {
+  __shared__ float red[32];
+  float lmax = 0.f;
+  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < WW; pix += gridDim.x * blockDim.x) {
+    float pint = 0.f;
+    for (int k = 0; k < M; ++k) pint += cabs2(P[(size_t)k * WW + pix]);
+    lmax = fmaxf(lmax, pint);
+  }
+  lmax = block_max(lmax, red);
+  if (threadIdx.x == 0) pmax_part[blockIdx.x] = lmax;
+}
+
+__global__ void __launch_bounds__(1024)
+k_err_reduce(const float* __restrict__ part, size_t n, double inv_sumI, float* out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (float)(red[0] * inv_sumI);
+}
+
+// Model intensities: forward column DFTs after pass A, S written out.
+template <int W>
+__global__ void __launch_bounds__(512)
+k_cols_intensity(const float2* __restrict__ scratch, int M, int CB,
+                 const int* __restrict__ ids, const float2* __restrict__ tw_g,
+                 float inv_w, float* __restrict__ out) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* tbuf = tw + W;
+  float* Sb = reinterpret_cast<float*>(tbuf + M * CB * G::LP);
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  const int lp = blockIdx.y, c0 = blockIdx.x * CB;
+  const int c = threadIdx.x % CB, rest = threadIdx.x / CB;
+  const int lane = rest % G::L, k = rest / G::L;
+  const bool act = k < M;
+  const int j = ids[lp];
+  const float2* col = scratch + ((size_t)lp * M + (act ? k : 0)) * W * W + c0 + c;
+  float2* lbuf = tbuf + ((act ? k : 0) * CB + c) * G::LP;
+  __syncthreads();
+  if (act && lane < G::N2) {
+    float2 v[G::N1];
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = col[(size_t)(G::N2 * n1 + lane) * W];
+    fwd_step1<W>(v, lane, tw, lbuf);
+  }
+  __syncthreads();
+  if (act && lane < G::N1) {
+    float2 z[G::N2];
+    fwd_step3<W>(z, lane, lbuf);
+#pragma unroll
+    for (int k2 = 0; k2 < G::N2; ++k2)
+      Sb[(k * CB + c) * W + lane + G::N1 * k2] = cabs2(z[k2]);
+  }
+  __syncthreads();
+  const float f2 = inv_w * inv_w;
+  for (int e = threadIdx.x; e < CB * W; e += blockDim.x) {
+    const int u = e / CB, cl = e - u * CB;
+    float s = 0.f;
+    for (int kk = 0; kk < M; ++kk) s += Sb[(kk * CB + cl) * W + u];
+    const int iu = (u + W / 2) % W, iv = (c0 + cl + W / 2) % W;
+    out[((size_t)j * W + iu) * W + iv] = s * f2;
+  }
+}
+
+// Plain batched 2-D DFT through the same line steps (rows, then columns).
+template <int W, bool INV>
+__global__ void __launch_bounds__(256) k_fft_rows(float2* __restrict__ data, int nrows) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* tbuf = tw + W;
+  const int lines = blockDim.x / G::L;
+  for (int e = threadIdx.x; e < W; e += blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * e / W, &sn, &cs);
+    tw[e] = make_float2((float)cs, (float)sn);
+  }
+  __syncthreads();
+  const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
+  const int row = blockIdx.x * lines + line;
+  const bool act = line < lines && row < nrows;
+  float2* x = data + (size_t)(act ? row : 0) * W;
+  float2* lbuf = tbuf + line * G::LP;
+  if (!INV) {
+    if (act && lane < G::N2) {
+      float2 v[G::N1];
+      for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = x[G::N2 * n1 + lane];
+      fwd_step1<W>(v, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (act && lane < G::N1) {
+      float2 z[G::N2];
+      fwd_step3<W>(z, lane, lbuf);
+      for (int k2 = 0; k2 < G::N2; ++k2) x[lane + G::N1 * k2] = z[k2];
+    }
+  } else {
+    if (act && lane < G::N1) {
+      float2 z[G::N2];
+      for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = x[lane + G::N1 * k2];
+      inv_stepA<W>(z, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (act && lane < G::N2) {
+      float2 v[G::N1];
+      inv_stepB<W>(v, lane, lbuf);
+      for (int n1 = 0; n1 < G::N1; ++n1) x[G::N2 * n1 + lane] = v[n1];
+    }
+  }
+}
+
+template <int W, bool INV>
+__global__ void __launch_bounds__(256) k_fft_cols(float2* __restrict__ data, int CB) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* tbuf = tw + W;
+  for (int e = threadIdx.x; e < W; e += blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * e / W, &sn, &cs);
+    tw[e] = make_float2((float)cs, (float)sn);
+  }
+  __syncthreads();
+  const int c = threadIdx.x % CB, lane = threadIdx.x / CB;  // lanes >= L stay idle
+  float2* col = data + (size_t)blockIdx.y * W * W + blockIdx.x * CB + c;
+  float2* lbuf = tbuf + c * G::LP;
+  if (!INV) {
+    if (lane < G::N2) {
+      float2 v[G::N1];
+      for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = col[(size_t)(G::N2 * n1 + lane) * W];
+      fwd_step1<W>(v, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (lane < G::N1) {
+      float2 z[G::N2];
+      fwd_step3<W>(z, lane, lbuf);
+      for (int k2 = 0; k2 < G::N2; ++k2) col[(size_t)(lane + G::N1 * k2) * W] = z[k2];
+    }
+  } else {
+    if (lane < G::N1) {
+      float2 z[G::N2];
+      for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = col[(size_t)(lane + G::N1 * k2) * W];
+      inv_stepA<W>(z, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (lane < G::N2) {
+      float2 v[G::N1];
+      inv_stepB<W>(v, lane, lbuf);
+      for (int n1 = 0; n1 < G::N1; ++n1) col[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
+    }
+  }
+}
+
+__global__ void k_finite(const float* __restrict__ p, size_t n, int* flag) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(p[i])) {
+      *flag = 1;
+      return;
+    }
+}
+
+int pow2_floor(int v) {
+  int p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+int round32(int v) { return (v + 31) / 32 * 32; }
+
+template <int W> void geo(int& L, int& LP) {
+  L = Line<W>::L;
+  LP = Line<W>::LP;
+}
+
+}  // namespace
+
+bool supported_W(int W) {
+  return W == 32 || W == 64 || W == 96 || W == 128 || W == 192 || W == 256;
+}
+
+#define PTY_DISPATCH_W(W, ...)                               \
+  switch (W) {                                               \
+    case 32: { constexpr int WW = 32; __VA_ARGS__; } break;   \
+    case 64: { constexpr int WW = 64; __VA_ARGS__; } break;   \
+    case 96: { constexpr int WW = 96; __VA_ARGS__; } break;   \
+    case 128: { constexpr int WW = 128; __VA_ARGS__; } break; \
+    case 192: { constexpr int WW = 192; __VA_ARGS__; } break; \
+    case 256: { constexpr int WW = 256; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;                   \
+  }
+
+Tiling make_tiling(int W, int M) {
+  Tiling t{};
+  t.W = W;
+  t.M = M;
+  int L = 16, LP = W;
+  switch (W) {
+    case 32: geo<32>(L, LP); break;
+    case 64: geo<64>(L, LP); break;
+    case 96: geo<96>(L, LP); break;
+    case 128: geo<128>(L, LP); break;
+    case 192: geo<192>(L, LP); break;
+    default: geo<256>(L, LP); break;
+  }
+  int R = pow2_floor(std::max(1, 256 / (M * L)));
+  R = std::min(R, 16);
+  while (W % R) R /= 2;
+  t.R = R;
+  t.ppc = 4;
+  int CB = pow2_floor(std::max(1, 512 / (M * L)));
+  CB = std::max(2, std::min(16, CB));  // M * CB * L <= 512 threads
+  while ((W / 2) % CB) CB /= 2;
+  t.CB = CB;
+  t.thrA = round32(M * R * L);
+  t.thrC = t.thrA;
+  t.thrB = round32(M * CB * L);
+  t.smA = (size_t)(W + M * R * W + M * R * LP) * sizeof(float2);
+  t.smB = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
+  t.smI = t.smB;
+  const int TB = std::max(M * R * LP, M * R * W);
+  t.smC = (size_t)(W + M * R * W + TB + M * R * W) * sizeof(float2) +
+          (size_t)2 * R * W * sizeof(float);
+  t.n_pmax = std::max(1, std::min(64, W * W / 1024));
+  return t;
+}
+
+cudaError_t set_smem_limits(const Tiling& t) {
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(t.W, {
+    e = cudaFuncSetAttribute(k_rows_fwd<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smA);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cols<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smB);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_rows_inv<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smC);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cols_intensity<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smI);
+  });
+  return e;
+}
+
+void make_twiddles(int W, float2* out) {
+  const double pi = 3.14159265358979323846;
+  for (int m = 0; m < W; ++m) {
+    const double th = -2.0 * pi * (double)m / (double)W;
+    out[m] = make_float2((float)std::cos(th), (float)std::sin(th));
+  }
+}
+
+cudaError_t launch_rows_fwd(const Tiling& t, const float2* O, int Hx, const float2* P,
+                            const int* ids, const int2* corners, int npatch,
+                            const float2* tw, float2* scratch, float* omax_part,
+                            cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
+  PTY_DISPATCH_W(t.W, (k_rows_fwd<WW><<<grid, t.thrA, t.smA, s>>>(
+                          O, Hx, P, t.M, t.R, t.ppc, ids, corners, npatch, tw,
+                          scratch, omax_part)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
+                        const int* ids, int npatch, const float2* tw, float inv_w,
+                        float eps, float* err_part, cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  dim3 grid(t.W / t.CB, npatch);
+  PTY_DISPATCH_W(t.W, (k_cols<WW><<<grid, t.thrB, t.smB, s>>>(
+                          scratch, t.M, t.CB, I, ids, tw, inv_w, eps, err_part)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
+                            const int* ids, const int2* corners, int npatch,
+                            const float2* scratch, const float* omax_part,
+                            const float* pmax_part, const float2* tw,
+                            const UpdArgs& a, float2* pnum, float* pden,
+                            float* osum, int accumulate, cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
+  PTY_DISPATCH_W(t.W, (k_rows_inv<WW><<<grid, t.thrC, t.smC, s>>>(
+                          O, Hx, P, t.M, t.R, t.ppc, ids, corners, npatch, scratch,
+                          omax_part, pmax_part, t.n_pmax, tw, a, pnum, pden, osum,
+                          accumulate)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
+                               const float* pden, const float* osum, int nslots,
+                               float alpha_P, float reg_eps, float* pmax_part,
+                               cudaStream_t s) {
+  k_probe_apply<<<t.n_pmax, 256, 0, s>>>(P, t.M, t.W * t.W, pnum, pden, osum, nslots,
+                                         alpha_P, reg_eps, pmax_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pmax(const Tiling& t, const float2* P, float* pmax_part, cudaStream_t s) {
+  k_pmax<<<t.n_pmax, 256, 0, s>>>(P, t.M, t.W * t.W, pmax_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI, float* out,
+                              cudaStream_t s) {
+  k_err_reduce<<<1, 1024, 0, s>>>(err_part, n, inv_sumI, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols_intensity(const Tiling& t, const float2* scratch, const int* ids,
+                                  int npatch, const float2* tw, float inv_w, float* out,
+                                  cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  dim3 grid(t.W / t.CB, npatch);
+  PTY_DISPATCH_W(t.W, (k_cols_intensity<WW><<<grid, t.thrB, t.smI, s>>>(
+                          scratch, t.M, t.CB, ids, tw, inv_w, out)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft2(void* data, int W, int batch, int inverse, const float2*,
+                        cudaStream_t s) {
+  float2* d = static_cast<float2*>(data);
+  const int nrows = W * batch;
+  PTY_DISPATCH_W(W, {
+    using G = Line<WW>;
+    const int lines = 256 / G::L;
+    const dim3 gr((nrows + lines - 1) / lines);
+    const size_t smr = (size_t)(WW + lines * G::LP) * sizeof(float2);
+    const int CB = pow2_floor(256 / G::L);
+    const dim3 gc(WW / CB, batch);
+    const size_t smc = (size_t)(WW + CB * G::LP) * sizeof(float2);
+    if (!inverse) {
+      k_fft_rows<WW, false><<<gr, 256, smr, s>>>(d, nrows);
+      k_fft_cols<WW, false><<<gc, 256, smc, s>>>(d, CB);
+    } else {
+      k_fft_rows<WW, true><<<gr, 256, smr, s>>>(d, nrows);
+      k_fft_cols<WW, true><<<gc, 256, smc, s>>>(d, CB);
+    }
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finite_check(const float* p, size_t n, int* flag, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_finite<<<296, 256, 0, s>>>(p, n, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace pty

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libpty (include/pty.h): argument marshalling only.
+
+Every step of the reconstruction runs in the library's CUDA kernels; this
+module converts torch tensors / NumPy arrays to pointers, picks the memory
+kind, and raises ``PtyError`` on a non-zero status.  Importing it fails
+loudly when ``libpty.so`` has not been built: there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpty.so")
+
+PTY_OK, PTY_EINVAL, PTY_ENOMEM, PTY_ECUDA, PTY_EDATA, PTY_ETIMEOUT, PTY_ESTATE = range(7)
+MEM_HOST, MEM_DEVICE = 0, 1
+ERR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EDATA", 5: "ETIMEOUT", 6: "ESTATE"}
+
+c_int, c_float, c_void_p, c_size_t = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+c_int_p = ctypes.POINTER(ctypes.c_int)
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p, c_void_p)
+
+
+class PtyError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (ERR_NAMES.get(code, code), msg))
+        self.code = code
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("W", c_int), ("M", c_int), ("N", c_int), ("Hy", c_int), ("Hx", c_int),
+                ("stream", c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", c_void_p), ("scratch_bytes", c_size_t), ("flags", c_int)]
+
+
+class RpieParams(ctypes.Structure):
+    _fields_ = [("alpha_O", c_float), ("alpha_P", c_float), ("beta", c_float), ("gamma", c_float),
+                ("eps", c_float), ("reg_eps", c_float), ("max_group", c_int),
+                ("update_probe", c_int)]
+
+
+class RefineParams(ctypes.Structure):
+    _fields_ = [("upsample", c_int), ("lr", c_float), ("b1", c_float), ("b2", c_float),
+                ("eps", c_float), ("start_iter", c_int), ("max_step", c_float)]
+
+
+def rpie_params(alpha_O=1.0, alpha_P=1.0, beta=1.0, gamma=0.1, eps=1.0, reg_eps=1e-12,
+                max_group=0, update_probe=True):
+    return RpieParams(alpha_O, alpha_P, beta, gamma, eps, reg_eps, max_group, int(update_probe))
+
+
+def refine_params(upsample=20, lr=0.5, b1=0.9, b2=0.999, eps=1e-8, start_iter=0, max_step=0.0):
+    return RefineParams(upsample, lr, b1, b2, eps, start_iter, max_step)
+
+
+_SIGS = {
+    "pty_last_error": (ctypes.c_char_p, []),
+    "pty_abi_version": (c_int, []),
+    "pty_init_problem": (c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(c_void_p)]),
+    "pty_destroy": (c_int, [c_void_p]),
+    "pty_set_data": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "pty_set_scan_order": (c_int, [c_void_p, c_void_p]),
+    "pty_run_iterations": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams), c_void_p]),
+    "pty_refine_positions": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams),
+                                     ctypes.POINTER(RefineParams), c_void_p, c_void_p]),
+    "pty_run_groups": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(RpieParams), c_void_p]),
+    "pty_get_groups": (c_int, [c_void_p, c_int_p, c_void_p, c_void_p]),
+    "pty_get_object": (c_int, [c_void_p, c_void_p, c_int]),
+    "pty_set_object": (c_int, [c_void_p, c_void_p, c_int]),
+    "pty_get_probe": (c_int, [c_void_p, c_void_p, c_int]),
+    "pty_set_probe": (c_int, [c_void_p, c_void_p, c_int]),
+    "pty_get_positions": (c_int, [c_void_p, c_void_p, c_int]),
+    "pty_set_positions": (c_int, [c_void_p, c_void_p, c_int]),
+    "pty_get_adam_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int_p, c_int_p, c_int]),
+    "pty_set_adam_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int]),
+    "pty_model_intensities": (c_int, [c_void_p, c_void_p, c_int]),
+    "pty_group_positions": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                    c_int_p]),
+    "pty_fft2": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libpty.so once; raises ImportError if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libpty.so is not built (run python -m paper_2205_04295_b300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != PTY_OK:
+        raise PtyError(rc, lib().pty_last_error().decode())
+
+
+# ------------------------------------------------------------ marshalling
+def _ptr(x, dtype):
+    """(pointer, mem_kind, keepalive) for a torch tensor or NumPy array."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != dtype[1]:
+                raise TypeError("expected %s, got %s" % (dtype[1], x.dtype))
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return x.data_ptr(), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype[0])
+    return a.ctypes.data, MEM_HOST, a
+
+
+def _dt(name):
+    import torch
+    return {"u16": (np.uint16, torch.uint16), "f32": (np.float32, torch.float32),
+            "c64": (np.complex64, torch.complex64), "i32": (np.int32, torch.int32)}[name]
+
+
+def group_positions(pos, W, max_group=0, order=None):
+    """Greedy disjoint grouping on the host (a C-ABI call that needs no GPU).
+
+    Returns a list of int32 arrays of position indices."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    N = len(pos)
+    gptr = np.zeros(N + 1, np.int32)
+    gpos = np.zeros(N, np.int32)
+    ng = ctypes.c_int(0)
+    od = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    check(lib().pty_group_positions(pos.ctypes.data, N, W, max_group,
+                                    None if od is None else od.ctypes.data,
+                                    gptr.ctypes.data, gpos.ctypes.data, ctypes.byref(ng)))
+    return [gpos[gptr[g]:gptr[g + 1]].copy() for g in range(ng.value)]
+
+
+def fft2_(x, inverse=False):
+    """In-place unnormalised 2-D DFT of a contiguous CUDA complex64 tensor (..., W, W)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.complex64 and x.is_contiguous()
+    W = x.shape[-1]
+    batch = x.numel() // (W * W)
+    check(lib().pty_fft2(x.data_ptr(), W, batch, int(inverse),
+                         torch.cuda.current_stream(x.device).cuda_stream))
+    return x
+
+
+class Problem:
+    """One reconstruction problem (a pty_handle) on the current CUDA device."""
+
+    def __init__(self, W, M, N, Hy, Hx, stream=None, scratch_bytes=0):
+        import torch
+        self.W, self.M, self.N, self.Hy, self.Hx = W, M, N, Hy, Hx
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        d = ProblemDesc(W, M, N, Hy, Hx, c_void_p(stream.cuda_stream), ALLOC_FN(), FREE_FN(),
+                        None, scratch_bytes, 0)
+        h = c_void_p()
+        check(lib().pty_init_problem(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pty_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- data
+    def set_data(self, I, pos, O0, P0):
+        pI, k1, a1 = _ptr(I, _dt("u16"))
+        pp, k2, a2 = _ptr(pos, _dt("f32"))
+        pO, k3, a3 = _ptr(O0, _dt("c64"))
+        pP, k4, a4 = _ptr(P0, _dt("c64"))
+        if len({k1, k2, k3, k4}) != 1:
+            raise ValueError("all of I, pos, O0, P0 must live in the same memory (host or device)")
+        check(lib().pty_set_data(self.h, pI, pp, pO, pP, k1))
+
+    def set_scan_order(self, order):
+        if order is None:
+            check(lib().pty_set_scan_order(self.h, None))
+        else:
+            o = np.ascontiguousarray(order, dtype=np.int32)
+            check(lib().pty_set_scan_order(self.h, o.ctypes.data))
+
+    # -- iterations
+    def run(self, n_iter, params=None, errors=True):
+        params = params or rpie_params()
+        err = np.zeros(max(n_iter, 1), np.float32)
+        check(lib().pty_run_iterations(self.h, n_iter, ctypes.byref(params),
+                                       err.ctypes.data if errors else None))
+        return err[:n_iter] if errors else None
+
+    def refine(self, n_iter, params=None, rparams=None, errors=True, shifts=False):
+        params = params or rpie_params()
+        rparams = rparams or refine_params()
+        err = np.zeros(max(n_iter, 1), np.float32)
+        sh = np.zeros((self.N, 2), np.float32)
+        check(lib().pty_refine_positions(self.h, n_iter, ctypes.byref(params), ctypes.byref(rparams),
+                                         err.ctypes.data if errors else None,
+                                         sh.ctypes.data if shifts else None))
+        out = err[:n_iter] if errors else None
+        return (out, sh) if shifts else out
+
+    def run_groups(self, g0, g1, params=None):
+        params = params or rpie_params()
+        e = np.zeros(1, np.float32)
+        check(lib().pty_run_groups(self.h, g0, g1, ctypes.byref(params), e.ctypes.data))
+        return float(e[0])
+
+    def groups(self):
+        ng = ctypes.c_int(0)
+        check(lib().pty_get_groups(self.h, ctypes.byref(ng), None, None))
+        gptr = np.zeros(ng.value + 1, np.int32)
+        gpos = np.zeros(self.N, np.int32)
+        check(lib().pty_get_groups(self.h, ctypes.byref(ng), gptr.ctypes.data, gpos.ctypes.data))
+        return [gpos[gptr[g]:gptr[g + 1]].copy() for g in range(ng.value)]
+
+    # -- copies (device tensors out)
+    def _get(self, fn, shape, dt, device=True):
+        import torch
+        if device:
+            t = torch.empty(shape, dtype=dt[1], device="cuda")
+            check(fn(self.h, t.data_ptr(), MEM_DEVICE))
+            return t
+        a = np.empty(shape, dtype=dt[0])
+        check(fn(self.h, a.ctypes.data, MEM_HOST))
+        return a
+
+    def object(self, device=True):
+        return self._get(lib().pty_get_object, (self.Hy, self.Hx), _dt("c64"), device)
+
+    def probe(self, device=True):
+        return self._get(lib().pty_get_probe, (self.M, self.W, self.W), _dt("c64"), device)
+
+    def positions(self, device=True):
+        return self._get(lib().pty_get_positions, (self.N, 2), _dt("f32"), device)
+
+    def model_intensities(self, device=True):
+        return self._get(lib().pty_model_intensities, (self.N, self.W, self.W), _dt("f32"), device)
+
+    def set_object(self, O):
+        p, k, a = _ptr(O, _dt("c64"))
+        check(lib().pty_set_object(self.h, p, k))
+
+    def set_probe(self, P):
+        p, k, a = _ptr(P, _dt("c64"))
+        check(lib().pty_set_probe(self.h, p, k))
+
+    def set_positions(self, pos):
+        p, k, a = _ptr(pos, _dt("f32"))
+        check(lib().pty_set_positions(self.h, p, k))
+
+    def adam_state(self):
+        m = np.zeros((self.N, 2), np.float32)
+        v = np.zeros((self.N, 2), np.float32)
+        t, it = ctypes.c_int(0), ctypes.c_int(0)
+        check(lib().pty_get_adam_state(self.h, m.ctypes.data, v.ctypes.data, ctypes.byref(t),
+                                       ctypes.byref(it), MEM_HOST))
+        return m, v, t.value, it.value
+
+    def set_adam_state(self, m, v, t, it):
+        m = np.ascontiguousarray(m, np.float32)
+        v = np.ascontiguousarray(v, np.float32)
+        check(lib().pty_set_adam_state(self.h, m.ctypes.data, v.ctypes.data, t, it, MEM_HOST))

@@ -1,0 +1,213 @@
+"""Parity of the CUDA M-rPIE path with the FP64 oracle on the same seeded
+inputs and the same grouped schedule.
+
+Tolerances: relative L2 (||a-b|| / ||b|| over whole arrays) <= 1e-5 for the
+object, the probe and the model intensities after one iteration, <= 1e-3
+after many; the reported error within 1e-5 relative."""
+import numpy as np
+import pytest
+
+from helpers import build, rel_l2, to_host
+from oracle import model, rpie
+from paper_2205_04295_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL1 = 1e-5
+
+
+def gpu_problem(wl, d, scratch_bytes=0):
+    from paper_2205_04295_b300 import pty
+    prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx, scratch_bytes=scratch_bytes)
+    prob.set_data(d["I"], d["pos"], d["O0"], d["P0"])
+    return prob
+
+
+def params_pair(**kw):
+    from paper_2205_04295_b300 import pty
+    return pty.rpie_params(**kw), rpie.RPIEParams(**kw)
+
+
+def check_one_iteration(wl, d, scratch_bytes=0, **kw):
+    pg, po = params_pair(**kw)
+    prob = gpu_problem(wl, d, scratch_bytes)
+    eg = prob.run(1, pg)[0]
+    st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+    eo = rpie.iterate(st, d["I"], po)
+    Og, Pg = prob.object(False), prob.probe(False)
+    assert rel_l2(Og, st.O) <= TOL1
+    assert rel_l2(Pg, st.P) <= TOL1
+    # the changes themselves (the unscanned object stays 1 and dilutes the above)
+    assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= 2e-4
+    assert rel_l2(Pg - d["P0"], st.P - d["P0"]) <= 2e-4
+    Ig = prob.model_intensities(False)
+    Io = model.model_intensities(st.O, st.P, d["pos"])
+    assert rel_l2(Ig, Io) <= TOL1
+    assert abs(eg - eo) <= TOL1 * eo
+    return prob, st
+
+
+CASES = {
+    "w32_m2": lambda: synth.tiny(W=32, M=2, ny=5, nx=5, step=6.0),
+    "w64_m1_plain": lambda: synth.plain_rpie_64(),
+    "w96_m2": lambda: synth.tiny(W=96, M=2, ny=3, nx=4, step=20.0, seed=3),
+    "w128_m3": lambda: synth.tiny(W=128, M=3, ny=3, nx=3, step=24.0, seed=4, photons=1e6),
+    "w192_m2": lambda: synth.tiny(W=192, M=2, ny=2, nx=3, step=40.0, seed=5),
+    "w256_m5": lambda: synth.tiny(W=256, M=5, ny=2, nx=3, step=48.0, seed=6, photons=1e6),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_one_iteration_parity(case):
+    wl = CASES[case]()
+    check_one_iteration(wl, build(wl))
+
+
+def test_ragged_chunks_and_regularisers():
+    # scratch of 3 patches: every group splits into chunks with a ragged tail
+    wl = synth.tiny(W=32, M=3, ny=7, nx=6, step=5.0, seed=11, jitter=1.5)
+    d = build(wl)
+    check_one_iteration(wl, d, scratch_bytes=3 * 3 * 32 * 32 * 8, alpha_O=0.7, alpha_P=0.6,
+                        beta=0.4, gamma=0.25)
+
+
+def test_sequential_mode_and_fixed_probe():
+    wl = synth.tiny(W=32, M=2, ny=4, nx=4, step=6.0, seed=12)
+    d = build(wl)
+    check_one_iteration(wl, d, max_group=1)
+    check_one_iteration(wl, d, update_probe=False)
+
+
+def test_plain_rpie_20_iterations():
+    wl = synth.plain_rpie_64()
+    d = build(wl)
+    pg, po = params_pair()
+    prob = gpu_problem(wl, d)
+    eg = prob.run(wl.n_iter, pg)
+    st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+    eo = rpie.run(st, d["I"], po, wl.n_iter)
+    assert rel_l2(prob.object(False), st.O) <= 1e-3
+    assert rel_l2(prob.probe(False), st.P) <= 1e-3
+    np.testing.assert_allclose(eg, eo, rtol=1e-3)
+    assert eo[-1] < eo[0]
+
+
+def test_zero_step_leaves_state_bitwise():
+    wl = synth.tiny(W=64, M=2, ny=3, nx=3, step=10.0, seed=13)
+    d = build(wl)
+    from paper_2205_04295_b300 import pty
+    prob = gpu_problem(wl, d)
+    prob.run(2, pty.rpie_params(alpha_O=0.0, alpha_P=0.0))
+    np.testing.assert_array_equal(prob.object(False), d["O0"])
+    np.testing.assert_array_equal(prob.probe(False), d["P0"])
+
+
+def test_runs_are_bitwise_deterministic():
+    wl = synth.tiny(W=64, M=3, ny=5, nx=5, step=8.0, seed=14)
+    d = build(wl)
+    outs = []
+    for _ in range(2):
+        prob = gpu_problem(wl, d)
+        e = prob.run(3)
+        outs.append((prob.object(False), prob.probe(False), e))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_edge_cases_single_position_corner_and_dark_pattern():
+    wl = synth.tiny(W=32, M=1, ny=1, nx=1, step=1.0, seed=15)
+    d = build(wl)
+    check_one_iteration(wl, d)
+    # a crop touching the far corner of the object
+    wl = synth.tiny(W=32, M=2, ny=2, nx=2, step=10.0, seed=16)
+    d = build(wl)
+    d["pos"][-1] = [wl.Hy - wl.W, wl.Hx - wl.W]
+    check_one_iteration(wl, d)
+    # an all-dark pattern: the object update is well defined
+    d["I"][0] = 0
+    check_one_iteration(wl, d, update_probe=False)
+
+
+def test_dark_pattern_with_probe_update_stays_finite():
+    # A dark pattern alone in its group drives an ePIE-like probe step
+    # (beta = 1) to exactly zero in FP32; zero denominators skip the update
+    # instead of producing NaN.
+    from paper_2205_04295_b300 import pty
+    wl = synth.tiny(W=32, M=2, ny=2, nx=2, step=10.0, seed=16)
+    d = build(wl)
+    d["I"][0] = 0
+    prob = gpu_problem(wl, d)
+    prob.run(2, pty.rpie_params())
+    assert np.all(np.isfinite(prob.object(False)))
+    assert np.all(np.isfinite(prob.probe(False)))
+
+
+def test_error_codes():
+    from paper_2205_04295_b300 import pty
+    wl = synth.tiny(W=32, M=1, ny=2, nx=2, step=6.0, seed=17)
+    d = build(wl)
+    prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
+    with pytest.raises(pty.PtyError) as e:
+        prob.run(1)
+    assert e.value.code == pty.PTY_ESTATE
+    bad = d["pos"].copy()
+    bad[0] = [wl.Hy - wl.W + 1, 0]
+    with pytest.raises(pty.PtyError) as e:
+        prob.set_data(d["I"], bad, d["O0"], d["P0"])
+    assert e.value.code == pty.PTY_EDATA
+    O = d["O0"].copy()
+    O[3, 4] = np.nan
+    with pytest.raises(pty.PtyError) as e:
+        prob.set_data(d["I"], d["pos"], O, d["P0"])
+    assert e.value.code == pty.PTY_EDATA
+    with pytest.raises(pty.PtyError) as e:
+        pty.Problem(100, 1, 4, 200, 200)
+    assert e.value.code == pty.PTY_EINVAL
+
+
+def test_device_inputs_equal_host_inputs():
+    import torch
+    wl = synth.tiny(W=64, M=2, ny=3, nx=3, step=10.0, seed=18)
+    d = build(wl)
+    from paper_2205_04295_b300 import pty
+    a = gpu_problem(wl, d)
+    a.run(2)
+    b = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
+    b.set_data(torch.from_numpy(d["I"].astype(np.int32)).to(torch.uint16).cuda(),
+               torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["O0"]).cuda(),
+               torch.from_numpy(d["P0"]).cuda())
+    b.run(2)
+    np.testing.assert_array_equal(a.object(False), b.object(False))
+    np.testing.assert_array_equal(a.probe(False), b.probe(False))
+
+
+def test_full_size_spiral_sampled_groups():
+    """Full 256x256, 5-mode, 10^4-position spiral, 2800^2 object, in the
+    launch configuration the benchmark times: run the first two groups on the
+    GPU and the same two groups in the oracle, then compare whole arrays."""
+    import torch
+    wl = synth.spiral_256()
+    d = synth.build(wl, device="cuda")
+    I_dev = synth.counts_u16(d["I"])
+    from paper_2205_04295_b300 import pty
+    prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
+    prob.set_data(I_dev, torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["O0"]).cuda(),
+                  torch.from_numpy(d["P0"]).cuda())
+    groups = prob.groups()
+    sel = np.concatenate(groups[:2])
+    I_host = np.zeros((wl.N, wl.W, wl.W), np.uint16)
+    I_host[sel] = to_host(I_dev.to(torch.int32)[torch.from_numpy(sel).long().cuda()]).astype(np.uint16)
+    eg = prob.run_groups(0, 2)
+    st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+    err = 0.0
+    corners = model.crop_corners(d["pos"])
+    po = rpie.RPIEParams()
+    for g in groups[:2]:
+        e, _, _ = rpie.rpie_group(st.O, st.P, I_host, corners, g, po)
+        err += e
+    total = float(I_dev.to(torch.int64).sum().item())
+    assert abs(eg - err / total) <= TOL1 * (err / total)
+    Og = prob.object(False)
+    assert rel_l2(Og, st.O) <= TOL1
+    assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= 2e-4
+    assert rel_l2(prob.probe(False), st.P) <= TOL1

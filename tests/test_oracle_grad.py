@@ -24,8 +24,13 @@ def central(f, x0, h):
 
 def test_gradient_matches_central_differences():
     O, P, pos, I = reduced_problem()
-    L, gO, gP, gpos = grad.loss_and_grad(O, P, pos, I, eps=0.0)
-    assert np.isclose(L, grad.loss(O, P, pos, I))
+    for delta in (0.0, 1.0):
+        check_fd(O, P, pos, I, delta)
+
+
+def check_fd(O, P, pos, I, delta):
+    L, gO, gP, gpos = grad.loss_and_grad(O, P, pos, I, delta=delta)
+    assert np.isclose(L, grad.loss(O, P, pos, I, delta=delta))
     h = 1e-6
     rng = np.random.default_rng(1)
     pix = [tuple(p) for p in rng.integers(2, 30, size=(12, 2))] + [(2, 3), (18, 21)]
@@ -34,7 +39,7 @@ def test_gradient_matches_central_differences():
             def f(t):
                 Oc = O.copy()
                 Oc[y, x] += t * unit
-                return grad.loss(Oc, P, pos, I)
+                return grad.loss(Oc, P, pos, I, delta=delta)
             fd = central(f, 0.0, h)
             assert np.isclose(fd, comp(gO[y, x]), rtol=1e-5, atol=1e-5 * (1 + abs(fd)))
     for (k, y, x) in [(0, 3, 4), (1, 8, 8), (0, 15, 0), (1, 0, 15)]:
@@ -42,7 +47,7 @@ def test_gradient_matches_central_differences():
             def f(t):
                 Pc = P.copy()
                 Pc[k, y, x] += t * unit
-                return grad.loss(O, Pc, pos, I)
+                return grad.loss(O, Pc, pos, I, delta=delta)
             fd = central(f, 0.0, h)
             assert np.isclose(fd, comp(gP[k, y, x]), rtol=1e-5, atol=1e-5 * (1 + abs(fd)))
     for j in range(len(pos)):
@@ -50,7 +55,7 @@ def test_gradient_matches_central_differences():
             def f(t):
                 pc = pos.copy()
                 pc[j, ax] += t
-                return grad.loss(O, P, pc, I)
+                return grad.loss(O, P, pc, I, delta=delta)
             fd = central(f, 0.0, h)
             assert np.isclose(fd, gpos[j, ax], rtol=1e-5, atol=1e-5 * (1 + abs(fd)))
 

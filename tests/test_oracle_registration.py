@@ -102,7 +102,7 @@ def test_refinement_moves_an_offset_position_toward_the_truth():
     sup = true.copy()
     sup[0] += np.array([1.5, -1.0])
     st = rpie.State.create(O, P[None], sup)
-    prm = rpie.RPIEParams(alpha_O=1.0, update_probe=False, gamma=0.5)
+    prm = rpie.RPIEParams(alpha_O=1.0, update_probe=False, gamma=0.5, eps=1e-6)
     rfn = rpie.RefineParams(upsample=20, lr=0.3)
     e0 = np.abs(st.pos[0] - true[0])
     for _ in range(4):

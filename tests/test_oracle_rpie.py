@@ -92,7 +92,7 @@ def test_update_numerators_are_minus_half_the_gradient():
     P = rng.normal(size=(M, W, W)) + 1j * rng.normal(size=(M, W, W))
     I = rng.uniform(0, 20, size=(1, W, W))
     pos = np.array([[3.0, 5.0]])
-    _, gO, gP, _ = grad.loss_and_grad(O, P, pos, I, eps=0.0)
+    _, gO, gP, _ = grad.loss_and_grad(O, P, pos, I, delta=0.0)
     Pmax = np.max(np.sum(np.abs(P) ** 2, 0))
     st = rpie.State.create(O, P, pos)
     rpie.iterate(st, I, rpie.RPIEParams(alpha_O=1.0, alpha_P=1.0, beta=1.0, gamma=1.0, eps=0.0, reg_eps=0.0))
@@ -154,6 +154,6 @@ def test_constraint_fixes_modulus_and_keeps_mode_ratios():
 def test_error_decreases_on_noise_free_data_with_true_probe():
     O, P, pos, I = consistent_problem(W=16, M=1, n=4, step=4, seed=11)
     st = rpie.State.create(np.ones_like(O), P, pos)
-    errs = rpie.run(st, I, rpie.RPIEParams(update_probe=False), 20)
+    errs = rpie.run(st, I, rpie.RPIEParams(update_probe=False, eps=1e-6), 20)
     assert errs[-1] < 0.2 * errs[0]
     assert all(b <= a * 1.05 for a, b in zip(errs, errs[1:]))
