@@ -148,6 +148,21 @@ int pty_get_adam_state(pty_handle* h, float* m, float* v, int* t, int* iter,
 int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t,
                        int iter, int mem_kind);
 
+/* Launch accounting, for benchmarks.  mode 0: count launches only (always
+ * on); 1: also time every kernel launch with CUDA events recorded on the
+ * handle's stream.  pty_get_stats synchronises the stream, fills *out with
+ * the totals since the last reset and, if reset != 0, zeroes them. */
+enum { PTY_K_ROWS_FWD = 0, PTY_K_COLS = 1, PTY_K_ROWS_INV = 2, PTY_K_PROBE = 3,
+       PTY_K_REDUCE = 4, PTY_K_REFINE = 5, PTY_K_GRAD = 6, PTY_K_OTHER = 7,
+       PTY_K_COUNT = 8 };
+typedef struct {
+  long long launches[PTY_K_COUNT];  /* kernel launches per kind */
+  double ms[PTY_K_COUNT];           /* summed device time per kind (mode 1) */
+  long long patches;                /* pattern updates processed */
+} pty_stats;
+int pty_profile(pty_handle* h, int mode);
+int pty_get_stats(pty_handle* h, pty_stats* out, int reset);
+
 /* Model intensities sum_p |F{P_p o_j}|^2 (Eq. 4) for all j at the current
  * O, P and rounded positions: N*W*W float, detector-centred. */
 int pty_model_intensities(pty_handle* h, float* dst, int mem_kind);

@@ -156,6 +156,55 @@ struct pty_handle {
   bool groups_valid = false;
   int grouped_max = -1;
   std::vector<void*> allocs;
+  // accounting
+  int prof_mode = 0;
+  long long n_launch[PTY_K_COUNT] = {0};
+  double ms[PTY_K_COUNT] = {0};
+  long long patches = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> event_pool;
+
+  cudaEvent_t take_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Launch-accounting bracket around one kernel launch of kind k.
+  struct Mark {
+    pty_handle* h;
+    int k;
+    cudaEvent_t a = nullptr;
+    Mark(pty_handle* hh, int kk) : h(hh), k(kk) {
+      ++h->n_launch[k];
+      if (h->prof_mode) {
+        a = h->take_event();
+        cudaEventRecord(a, h->stream);
+      }
+    }
+    ~Mark() {
+      if (a) {
+        cudaEvent_t b = h->take_event();
+        cudaEventRecord(b, h->stream);
+        h->pending.push_back({k, {a, b}});
+      }
+    }
+  };
+  void drain() {
+    for (auto& p : pending) {
+      float t = 0.f;
+      cudaEventSynchronize(p.second.second);
+      cudaEventElapsedTime(&t, p.second.first, p.second.second);
+      ms[p.first] += t;
+      event_pool.push_back(p.second.first);
+      event_pool.push_back(p.second.second);
+    }
+    pending.clear();
+  }
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -179,6 +228,8 @@ struct pty_handle {
   ~pty_handle() {
     if (stream) cudaStreamSynchronize(stream);
     else cudaDeviceSynchronize();
+    drain();
+    for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
     for (void* p : allocs) {
       if (ff) ff(p, stream, actx);
       else cudaFree(p);
@@ -253,19 +304,30 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p) {
   for (int c0 = 0; c0 < n; c0 += h->Qc) {
     const int nc = std::min(h->Qc, n - c0);
     const int* idc = ids + c0;
-    CU(pty::launch_rows_fwd(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, h->scratch,
-                            h->omax_part, h->stream));
-    CU(pty::launch_cols(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps, h->err_part,
-                        h->stream));
-    CU(pty::launch_rows_inv(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
-                            h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
-                            c0 > 0, h->stream));
+    {
+      pty_handle::Mark m(h, PTY_K_ROWS_FWD);
+      CU(pty::launch_rows_fwd(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, h->scratch,
+                              h->omax_part, h->stream));
+    }
+    {
+      pty_handle::Mark m(h, PTY_K_COLS);
+      CU(pty::launch_cols(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps,
+                          h->err_part, h->stream));
+    }
+    {
+      pty_handle::Mark m(h, PTY_K_ROWS_INV);
+      CU(pty::launch_rows_inv(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
+                              h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
+                              c0 > 0, h->stream));
+    }
   }
   if (p->update_probe) {
     const int used = (std::min(h->Qc, n) + h->tl.ppc - 1) / h->tl.ppc;
+    pty_handle::Mark m(h, PTY_K_PROBE);
     CU(pty::launch_probe_apply(h->tl, h->P, h->pnum, h->pden, h->osum, used, p->alpha_P,
                                p->reg_eps, h->pmax_part, h->stream));
   }
+  h->patches += n;
   return PTY_OK;
 }
 
@@ -445,7 +507,10 @@ int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, floa
     TRY(regroup(h, p->max_group));
     const int G = (int)h->gptr.size() - 1;
     for (int g = 0; g < G; ++g) TRY(run_group(h, g, p));
-    CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter + it, h->stream));
+    {
+      pty_handle::Mark m(h, PTY_K_REDUCE);
+      CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter + it, h->stream));
+    }
     ++h->iter;
   }
   if (err_out) {
@@ -617,6 +682,35 @@ int pty_model_intensities(pty_handle* h, float* dst, int mem_kind) {
     h->dfree(tmp);
   }
   return rc;
+}
+
+int pty_profile(pty_handle* h, int mode) {
+  g_err.clear();
+  if (!h) return fail(PTY_EINVAL, "null handle");
+  if (mode != 0 && mode != 1) return fail(PTY_EINVAL, "profile mode %d", mode);
+  h->prof_mode = mode;
+  return PTY_OK;
+}
+
+int pty_get_stats(pty_handle* h, pty_stats* out, int reset) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  if (!out) return fail(PTY_EINVAL, "null stats");
+  CU(cudaStreamSynchronize(h->stream));
+  h->drain();
+  for (int k = 0; k < PTY_K_COUNT; ++k) {
+    out->launches[k] = h->n_launch[k];
+    out->ms[k] = h->ms[k];
+  }
+  out->patches = h->patches;
+  if (reset) {
+    for (int k = 0; k < PTY_K_COUNT; ++k) {
+      h->n_launch[k] = 0;
+      h->ms[k] = 0;
+    }
+    h->patches = 0;
+  }
+  return PTY_OK;
 }
 
 int pty_group_positions(const float* pos, int N, int W, int max_group, const int32_t* order,

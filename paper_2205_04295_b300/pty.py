@@ -46,6 +46,19 @@ class RefineParams(ctypes.Structure):
                 ("eps", c_float), ("start_iter", c_int), ("max_step", c_float)]
 
 
+K_NAMES = ["rows_fwd", "cols", "rows_inv", "probe", "reduce", "refine", "grad", "other"]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8),
+                ("patches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {"launches": {k: int(self.launches[i]) for i, k in enumerate(K_NAMES)},
+                "ms": {k: float(self.ms[i]) for i, k in enumerate(K_NAMES)},
+                "patches": int(self.patches)}
+
+
 def rpie_params(alpha_O=1.0, alpha_P=1.0, beta=1.0, gamma=0.1, eps=1.0, reg_eps=1e-12,
                 max_group=0, update_probe=True):
     return RpieParams(alpha_O, alpha_P, beta, gamma, eps, reg_eps, max_group, int(update_probe))
@@ -79,6 +92,8 @@ _SIGS = {
     "pty_group_positions": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                     c_int_p]),
     "pty_fft2": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
+    "pty_profile": (c_int, [c_void_p, c_int]),
+    "pty_get_stats": (c_int, [c_void_p, ctypes.POINTER(Stats), c_int]),
 }
 
 _lib = None
@@ -280,6 +295,14 @@ class Problem:
         check(lib().pty_get_adam_state(self.h, m.ctypes.data, v.ctypes.data, ctypes.byref(t),
                                        ctypes.byref(it), MEM_HOST))
         return m, v, t.value, it.value
+
+    def profile(self, mode):
+        check(lib().pty_profile(self.h, int(mode)))
+
+    def stats(self, reset=False):
+        st = Stats()
+        check(lib().pty_get_stats(self.h, ctypes.byref(st), int(reset)))
+        return st.as_dict()
 
     def set_adam_state(self, m, v, t, it):
         m = np.ascontiguousarray(m, np.float32)
