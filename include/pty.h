@@ -167,6 +167,24 @@ int pty_get_stats(pty_handle* h, pty_stats* out, int reset);
  * O, P and rounded positions: N*W*W float, detector-centred. */
 int pty_model_intensities(pty_handle* h, float* dst, int mem_kind);
 
+/* Model intensities, as pty_model_intensities, for callers that may not
+ * allocate device memory at all (no counterpart in the paper: an interface
+ * choice of this library).  Needs no handle: O (Hy x Hx), P (M x W x W,
+ * complex64), pos (N x 2 float) and out (N x W x W float, detector-centred)
+ * are caller-owned DEVICE pointers; work is queued on `stream`.  It calls no
+ * allocator: its only intermediate lives in a fixed device array of
+ * PTY_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * process exit.  One pattern needs M*W*W*8 bytes of it; larger requests fail
+ * with PTY_EINVAL.  All calls share that array, so calls overlapping on the
+ * GPU race; serialise them.  The first call on each device resolves the
+ * array's device address (cudaGetSymbolAddress) and should come before any
+ * stream capture.  A pattern whose crop box leaves the object is written as
+ * NaN. */
+#define PTY_NOALLOC_SCRATCH_BYTES ((size_t)6 << 20)
+int pty_model_intensities_noalloc(const void* O, int Hy, int Hx, const void* P,
+                                  int M, int W, const float* pos, int N,
+                                  float* out, void* stream);
+
 /* Host-only greedy grouping (no GPU needed): positions pos (N*2, host),
  * boxes of side W, optional order (NULL = index order), max_group (0 =
  * unlimited).  Writes group_ptr (capacity N+1), group_pos (N), *n_groups.

@@ -124,6 +124,16 @@ bool valid_perm(const int32_t* order, int N) {
 
 }  // namespace
 
+int pty::set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 struct pty_handle {
   int W = 0, M = 0, N = 0, Hy = 0, Hx = 0;
   cudaStream_t stream = nullptr;

@@ -23,6 +23,9 @@ struct Tiling {
 };
 
 bool supported_W(int W);
+
+// Record a failure message for pty_last_error() on this thread; returns code.
+int set_error(int code, const char* fmt, ...);
 Tiling make_tiling(int W, int M);
 cudaError_t set_smem_limits(const Tiling& t);
 

@@ -93,6 +93,8 @@ _SIGS = {
                                     c_int_p]),
     "pty_fft2": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
     "pty_profile": (c_int, [c_void_p, c_int]),
+    "pty_model_intensities_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int,
+                                              c_void_p, c_int, c_void_p, c_void_p]),
     "pty_get_stats": (c_int, [c_void_p, ctypes.POINTER(Stats), c_int]),
 }
 
