@@ -124,6 +124,20 @@ int pty_set_scan_order(pty_handle* h, const int32_t* order);
 int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p,
                        float* err_out);
 
+/* n_iter iterations with XCORR_A registration of every updated crop and an
+ * Adam step of every position at the end of each iteration (once the
+ * handle's iteration count reaches r->start_iter).  Positions are clamped to
+ * keep the crops inside O.  shift_out (host, N*2, may be NULL) receives the
+ * last measured shift g_j = -argmax xcorr(o_j, o'_j). */
+int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
+                         const pty_refine_params* r, float* err_out,
+                         float* shift_out);
+
+/* Relative gap between the best and the second-best fine-grid value of each
+ * position's last registration, N floats: values near 0 flag near-ties whose
+ * argmax FP32 and FP64 may resolve differently. */
+int pty_get_refine_gaps(pty_handle* h, float* dst, int mem_kind);
+
 /* Run only groups [g_begin, g_end) of the current grouping, without touching
  * positions or the iteration counter (for sampled checks of one full-size
  * launch sequence).  err_out (host, may be NULL): one value, the error

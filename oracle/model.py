@@ -11,8 +11,8 @@ Readings (the paper leaves these open):
   at pixel (W/2, W/2), i.e. the stored pattern is ``fftshift`` of the
   unshifted |Psi|^2.
 * The crop box of position j has its top-left corner at
-  ``floor(pos_j + 0.5)`` (round half up), positions being (y, x) in object
-  pixels.
+  ``floor(pos_j + 0.5)`` (round half up) of the float32 position, positions
+  being (y, x) in object pixels.
 """
 import numpy as np
 
@@ -38,8 +38,12 @@ def from_detector(a):
 
 
 def crop_corners(pos):
-    """Integer top-left crop corners, floor(pos + 0.5), shape (N, 2) int64."""
-    pos = np.asarray(pos, dtype=np.float64)
+    """Integer top-left crop corners, floor(pos + 0.5), shape (N, 2) int64.
+
+    The rounding decides an integer, so it is taken on the float32 value of
+    the position (the precision positions are stored in), evaluated exactly.
+    """
+    pos = np.asarray(pos, dtype=np.float32).astype(np.float64)
     return np.floor(pos + 0.5).astype(np.int64)
 
 

@@ -18,6 +18,12 @@ Definitions used here (readings of a passage the paper keeps short):
 * fine grid: K = ceil(1.5 U) points per axis at s0 + (k - K//2)/U,
   k = 0..K-1; the result is the first maximum of |c|^2 on it (row-major).
 
+Precision of the decision: the argmax picks a quantised shift, so the
+values it compares are evaluated in float32/complex64 (``dtype``), the
+precision of the paper's PyTorch code and of the CUDA kernels; the DFTs of
+the two crops and their cross power are formed in complex128 first.  With
+``dtype=np.complex128`` everything is double.
+
 Written from the paper's description and the published method, not from any
 third-party code.
 """
@@ -36,7 +42,7 @@ def wrap(i, W):
     return i - W if i >= W // 2 else i
 
 
-def xcorr_peak(a, b, U):
+def xcorr_peak(a, b, U, dtype=np.complex64):
     """Peak (sy, sx) of the cross-correlation of b against a, to 1/U pixel.
 
     Returns ``(shift, gap)`` where ``shift`` is a float64 pair and ``gap`` is the
@@ -46,7 +52,7 @@ def xcorr_peak(a, b, U):
     a = np.asarray(a, dtype=np.complex128)
     b = np.asarray(b, dtype=np.complex128)
     Wy, Wx = a.shape
-    X = np.fft.fft2(b) * np.conj(np.fft.fft2(a))
+    X = (np.fft.fft2(b) * np.conj(np.fft.fft2(a))).astype(dtype)
     # coarse: c on the integer grid is W^2 * ifft2(X); the scale does not move the peak
     c = np.fft.ifft2(X)
     k = int(np.argmax(np.abs(c) ** 2))
@@ -58,8 +64,8 @@ def xcorr_peak(a, b, U):
     half = K // 2
     ys = sy + (np.arange(K) - half) / U
     xs = sx + (np.arange(K) - half) / U
-    Er = np.exp(2j * np.pi * np.outer(ys, signed_freqs(Wy)) / Wy)  # K x Wy
-    Ec = np.exp(2j * np.pi * np.outer(signed_freqs(Wx), xs) / Wx)  # Wx x K
+    Er = np.exp(2j * np.pi * np.outer(ys, signed_freqs(Wy)) / Wy).astype(dtype)  # K x Wy
+    Ec = np.exp(2j * np.pi * np.outer(signed_freqs(Wx), xs) / Wx).astype(dtype)  # Wx x K
     up = np.abs(Er @ X @ Ec) ** 2
     flat = up.ravel()
     k = int(np.argmax(flat))

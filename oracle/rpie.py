@@ -38,7 +38,7 @@ one Adam step at the end of the iteration (Eqs. 8-9, Algorithm 1) and the
 positions are clamped to keep the crop inside the object; regrouping happens
 at the start of the next iteration.
 """
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -81,7 +81,7 @@ class State:
     t: int = 0                # Adam steps taken
     it: int = 0               # iterations run
     last_shift: np.ndarray = None
-    gaps: list = field(default_factory=list)
+    gap: np.ndarray = None        # per position: relative best/second gap of the last registration
 
     @classmethod
     def create(cls, O0, P0, pos0):
@@ -89,7 +89,7 @@ class State:
         return cls(O=np.asarray(O0, dtype=np.complex128).copy(),
                    P=np.asarray(P0, dtype=np.complex128).copy(), pos=pos,
                    m=np.zeros_like(pos), v=np.zeros_like(pos),
-                   last_shift=np.zeros_like(pos))
+                   last_shift=np.zeros_like(pos), gap=np.ones(len(pos)))
 
 
 def rpie_group(O, P, I, corners, members, prm, U=0):
@@ -155,13 +155,12 @@ def iterate(state, I, prm, rfn=None, order=None, groups=None):
     corners = crop_corners(state.pos)
     err = 0.0
     g_meas = np.zeros_like(state.pos)
-    state.gaps = []
     for members in groups:
         e, sh, gaps = rpie_group(state.O, state.P, I, corners, members, prm, U)
         err += e
         if refine_on:
             g_meas[members] = -sh
-            state.gaps.extend(gaps)
+            state.gap[members] = gaps
     if refine_on:
         state.t += 1
         pos, state.m, state.v = adam_step(state.pos, state.m, state.v, g_meas,

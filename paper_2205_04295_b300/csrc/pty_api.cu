@@ -141,8 +141,13 @@ struct pty_handle {
   pty_free_fn ff = nullptr;
   void* actx = nullptr;
   int device = 0;
-  pty::Tiling tl{};
-  int Qc = 1, nslots = 1;
+  pty::Tiling tl{}, tlr{};   // plain and refining launch geometry
+  int Qc = 1, Qcr = 1, nslots = 1;
+  pty::RefGeo rg{};
+  float2* roots = nullptr;
+  int roots_U = 0;
+  float *cval = nullptr, *gap = nullptr;
+  int* cidx = nullptr;
   float inv_w = 1.f;
   // device state
   float2 *O = nullptr, *P = nullptr, *tw = nullptr, *scratch = nullptr, *pnum = nullptr;
@@ -307,34 +312,45 @@ pty::UpdArgs upd_args(const pty_rpie_params* p) {
   return pty::UpdArgs{p->alpha_O, p->alpha_P, p->beta, p->gamma, p->eps, p->reg_eps};
 }
 
-int run_group(pty_handle* h, int g, const pty_rpie_params* p) {
+int run_group(pty_handle* h, int g, const pty_rpie_params* p, bool refine = false) {
   const int n = h->gptr[g + 1] - h->gptr[g];
   const int* ids = h->gpos_d + h->gptr[g];
   const pty::UpdArgs a = upd_args(p);
-  for (int c0 = 0; c0 < n; c0 += h->Qc) {
-    const int nc = std::min(h->Qc, n - c0);
+  const pty::Tiling& tl = refine ? h->tlr : h->tl;
+  const int Qc = refine ? h->Qcr : h->Qc;
+  for (int c0 = 0; c0 < n; c0 += Qc) {
+    const int nc = std::min(Qc, n - c0);
     const int* idc = ids + c0;
     {
       pty_handle::Mark m(h, PTY_K_ROWS_FWD);
-      CU(pty::launch_rows_fwd(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, h->scratch,
+      CU(pty::launch_rows_fwd(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, h->scratch,
                               h->omax_part, h->stream));
     }
     {
       pty_handle::Mark m(h, PTY_K_COLS);
-      CU(pty::launch_cols(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps,
+      CU(pty::launch_cols(tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps,
                           h->err_part, h->stream));
     }
     {
       pty_handle::Mark m(h, PTY_K_ROWS_INV);
-      CU(pty::launch_rows_inv(h->tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
+      CU(pty::launch_rows_inv(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
                               h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
                               c0 > 0, h->stream));
     }
+    if (refine) {
+      pty_handle::Mark m(h, PTY_K_REFINE);
+      CU(pty::launch_xcorr_cols(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
+      CU(pty::launch_xcorr_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->cval, h->cidx,
+                                h->stream));
+      CU(pty::launch_updft(h->rg, h->scratch, tl.npl, h->M, idc, nc, h->cval, h->cidx,
+                           h->roots, h->shift, h->gap, h->stream));
+      h->n_launch[PTY_K_REFINE] += 2;
+    }
   }
   if (p->update_probe) {
-    const int used = (std::min(h->Qc, n) + h->tl.ppc - 1) / h->tl.ppc;
+    const int used = (std::min(Qc, n) + tl.ppc - 1) / tl.ppc;
     pty_handle::Mark m(h, PTY_K_PROBE);
-    CU(pty::launch_probe_apply(h->tl, h->P, h->pnum, h->pden, h->osum, used, p->alpha_P,
+    CU(pty::launch_probe_apply(tl, h->P, h->pnum, h->pden, h->osum, used, p->alpha_P,
                                p->reg_eps, h->pmax_part, h->stream));
   }
   h->patches += n;
@@ -398,26 +414,37 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
     cudaGetLastError();
     return bail(fail(PTY_ECUDA, "no CUDA device"));
   }
-  h->tl = pty::make_tiling(h->W, h->M);
+  h->tl = pty::make_tiling(h->W, h->M, false);
+  h->tlr = pty::make_tiling(h->W, h->M, true);
   if (cudaError_t e = pty::set_smem_limits(h->tl); e != cudaSuccess)
     return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
+  if (h->tlr.smA > 227 * 1024 || h->tlr.smB > 227 * 1024 || h->tlr.smC > 227 * 1024 ||
+      h->tl.smC > 227 * 1024)
+    return bail(fail(PTY_EINVAL, "W=%d with M=%d modes exceeds shared memory", h->W, h->M));
   const size_t W2 = (size_t)h->W * h->W;
   const size_t budget = d->scratch_bytes ? d->scratch_bytes : ((size_t)64 << 20);
-  h->Qc = (int)std::max<size_t>(1, budget / (W2 * h->M * sizeof(float2)));
+  h->Qc = (int)std::max<size_t>(1, budget / (W2 * h->tl.npl * sizeof(float2)));
   h->Qc = std::min(h->Qc, h->N);
-  h->nslots = (h->Qc + h->tl.ppc - 1) / h->tl.ppc;
+  h->Qcr = (int)std::max<size_t>(1, budget / (W2 * h->tlr.npl * sizeof(float2)));
+  h->Qcr = std::min(h->Qcr, h->N);
+  h->nslots = (std::max(h->Qc, h->Qcr) + h->tl.ppc - 1) / h->tl.ppc;
   h->inv_w = (float)(1.0 / h->W);
-  const int nrb = h->W / h->tl.R;
+  const int nrb = h->W / std::min(h->tl.R, h->tlr.R);
+  const size_t scratch_elems = std::max((size_t)h->Qc * h->tl.npl, (size_t)h->Qcr * h->tlr.npl) * W2;
+  const size_t nparts = (size_t)h->Qcr * h->W;  // >= Qcr * (W / RX)
   h->err_part_n = (size_t)h->N * (h->W / h->tl.CB);
   int rc = PTY_OK;
   if ((rc = alloc_into(h, h->O, (size_t)h->Hy * h->Hx)) ||
       (rc = alloc_into(h, h->P, (size_t)h->M * W2)) ||
       (rc = alloc_into(h, h->tw, (size_t)h->W)) ||
-      (rc = alloc_into(h, h->scratch, (size_t)h->Qc * h->M * W2)) ||
+      (rc = alloc_into(h, h->scratch, scratch_elems)) ||
+      (rc = alloc_into(h, h->cval, nparts)) ||
+      (rc = alloc_into(h, h->cidx, nparts)) ||
+      (rc = alloc_into(h, h->gap, (size_t)h->N)) ||
       (rc = alloc_into(h, h->pnum, (size_t)h->nslots * h->M * W2)) ||
       (rc = alloc_into(h, h->pden, (size_t)h->nslots * W2)) ||
       (rc = alloc_into(h, h->osum, (size_t)h->nslots)) ||
-      (rc = alloc_into(h, h->omax_part, (size_t)h->Qc * nrb)) ||
+      (rc = alloc_into(h, h->omax_part, (size_t)std::max(h->Qc, h->Qcr) * nrb)) ||
       (rc = alloc_into(h, h->err_part, h->err_part_n)) ||
       (rc = alloc_into(h, h->pmax_part, (size_t)h->tl.n_pmax)) ||
       (rc = alloc_into(h, h->I, (size_t)h->N * W2)) ||
@@ -528,6 +555,87 @@ int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, floa
                        h->stream));
     CU(cudaStreamSynchronize(h->stream));
   }
+  return PTY_OK;
+}
+
+int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
+                         const pty_refine_params* r, float* err_out, float* shift_out) {
+  g_err.clear();
+  TRY(check_handle(h, true));
+  TRY(check_params(p));
+  if (!r) return fail(PTY_EINVAL, "null refine params");
+  if (n_iter < 0) return fail(PTY_EINVAL, "n_iter < 0");
+  if (r->upsample < 1 || r->upsample > 40) return fail(PTY_EINVAL, "upsample %d outside 1..40", r->upsample);
+  if (!std::isfinite(r->lr) || !(r->b1 >= 0.f && r->b1 < 1.f) || !(r->b2 >= 0.f && r->b2 < 1.f) ||
+      !(r->eps >= 0.f) || !(r->max_step >= 0.f) || r->start_iter < 0)
+    return fail(PTY_EINVAL, "bad refine parameters");
+  if (r->upsample != h->roots_U) {
+    h->rg = pty::make_refgeo(h->W, r->upsample);
+    if (h->rg.smU > 227 * 1024) return fail(PTY_EINVAL, "upsample %d too large for W=%d", r->upsample, h->W);
+    CU(pty::set_refine_smem(h->rg));
+    CU(pty::set_smem_limits(h->tlr));
+    if (h->roots) {
+      CU(cudaStreamSynchronize(h->stream));
+      h->dfree(h->roots);
+      h->roots = nullptr;
+    }
+    std::vector<float2> roots((size_t)h->rg.U * h->W);
+    pty::make_up_roots(h->W, h->rg.U, roots.data());
+    TRY(alloc_into(h, h->roots, roots.size()));
+    CU(cudaMemcpyAsync(h->roots, roots.data(), sizeof(float2) * roots.size(),
+                       cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->roots_U = r->upsample;
+  }
+  if (n_iter == 0) return PTY_OK;
+  TRY(ensure_err_cap(h, n_iter));
+  const double inv = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
+  for (int it = 0; it < n_iter; ++it) {
+    TRY(regroup(h, p->max_group));
+    const bool on = h->iter >= r->start_iter;
+    if (on) CU(pty::set_smem_limits(h->tlr));
+    const int G = (int)h->gptr.size() - 1;
+    for (int g = 0; g < G; ++g) TRY(run_group(h, g, p, on));
+    {
+      pty_handle::Mark m(h, PTY_K_REDUCE);
+      CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter + it, h->stream));
+    }
+    if (on) {
+      ++h->adam_t;
+      const double bc1 = 1.0 - std::pow((double)r->b1, h->adam_t);
+      const double bc2 = 1.0 - std::pow((double)r->b2, h->adam_t);
+      {
+        pty_handle::Mark m(h, PTY_K_REFINE);
+        CU(pty::launch_adam(h->pos, h->am, h->av, h->shift, h->N, r->lr, r->b1, r->b2, r->eps,
+                            (float)bc1, (float)bc2, r->max_step, (float)(h->Hy - h->W),
+                            (float)(h->Hx - h->W), h->stream));
+      }
+      CU(cudaMemcpyAsync(h->pos_h.data(), h->pos, sizeof(float) * 2 * h->N,
+                         cudaMemcpyDeviceToHost, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      h->groups_valid = false;
+    }
+    ++h->iter;
+  }
+  if (err_out) {
+    CU(cudaMemcpyAsync(err_out, h->err_iter, sizeof(float) * n_iter, cudaMemcpyDeviceToHost,
+                       h->stream));
+  }
+  if (shift_out) {
+    CU(cudaMemcpyAsync(shift_out, h->shift, sizeof(float) * 2 * h->N, cudaMemcpyDeviceToHost,
+                       h->stream));
+  }
+  CU(cudaStreamSynchronize(h->stream));
+  return PTY_OK;
+}
+
+int pty_get_refine_gaps(pty_handle* h, float* dst, int mem_kind) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (!dst) return fail(PTY_EINVAL, "null destination");
+  CU(cudaMemcpyAsync(dst, h->gap, sizeof(float) * h->N, kind_out(mem_kind), h->stream));
+  if (mem_kind == PTY_MEM_HOST) CU(cudaStreamSynchronize(h->stream));
   return PTY_OK;
 }
 
@@ -674,8 +782,9 @@ int pty_model_intensities(pty_handle* h, float* dst, int mem_kind) {
   int rc = PTY_OK;
   for (int c0 = 0; c0 < h->N && rc == PTY_OK; c0 += h->Qc) {
     const int nc = std::min(h->Qc, h->N - c0);
-    cudaError_t e = pty::launch_rows_fwd(h->tl, h->O, h->Hx, h->P, h->iota + c0, h->corners, nc,
-                                         h->tw, h->scratch, h->omax_part, h->stream);
+    cudaError_t e = pty::launch_rows_fwd_plain(h->tl, h->O, h->Hx, h->P, h->iota + c0,
+                                               h->corners, nc, h->tw, h->scratch,
+                                               h->omax_part, h->stream);
     if (e == cudaSuccess)
       e = pty::launch_cols_intensity(h->tl, h->scratch, h->iota + c0, nc, h->tw, h->inv_w, out,
                                      h->stream);

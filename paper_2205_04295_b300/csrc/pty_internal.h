@@ -14,6 +14,9 @@ struct UpdArgs {
 // Launch geometry of the three passes for one (W, M).
 struct Tiling {
   int W, M;
+  int npl;       // far-field planes per patch in the scratch (M, or M + 2 refining)
+  int xo;        // 1: passes A/B also transform the crop itself (plane M)
+  int refine;    // 1: pass C also row-transforms the refined crop (plane M + 1)
   int R;         // rows per CTA, row passes
   int ppc;       // patches per CTA, row passes
   int CB;        // columns per CTA, column pass
@@ -26,7 +29,7 @@ bool supported_W(int W);
 
 // Record a failure message for pty_last_error() on this thread; returns code.
 int set_error(int code, const char* fmt, ...);
-Tiling make_tiling(int W, int M);
+Tiling make_tiling(int W, int M, bool refine = false);
 cudaError_t set_smem_limits(const Tiling& t);
 
 // Twiddle table w_W^m = exp(-2 pi i m / W), m = 0..W-1 (host, double -> float).
@@ -37,12 +40,16 @@ cudaError_t launch_rows_fwd(const Tiling& t, const float2* O, int Hx,
                             const float2* P, const int* ids, const int2* corners,
                             int npatch, const float2* tw, float2* scratch,
                             float* omax_part, cudaStream_t s);
+cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx,
+                                  const float2* P, const int* ids, const int2* corners,
+                                  int npatch, const float2* tw, float2* scratch,
+                                  float* omax_part, cudaStream_t s);
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
                         float eps, float* err_part, cudaStream_t s);
 cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             const int* ids, const int2* corners, int npatch,
-                            const float2* scratch, const float* omax_part,
+                            float2* scratch, const float* omax_part,
                             const float* pmax_part, const float2* tw,
                             const UpdArgs& a, float2* pnum, float* pden,
                             float* osum, int accumulate, cudaStream_t s);
@@ -57,6 +64,28 @@ cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
 cudaError_t launch_cols_intensity(const Tiling& t, const float2* scratch,
                                   const int* ids, int npatch, const float2* tw,
                                   float inv_w, float* out, cudaStream_t s);
+// ---- XCORR_A registration and the Adam step (pty_refine.cu) ---------------
+struct RefGeo {
+  int W, U, K;   // fine grid K = ceil(1.5 U) points per axis
+  int CBX, RX;   // columns / rows per CTA of the correlation passes
+  size_t smX, smR, smU;
+};
+RefGeo make_refgeo(int W, int U);
+cudaError_t set_refine_smem(const RefGeo& g);
+// roots exp(+2 pi i n / (U W)), n = 0..U W - 1 (host, double -> float)
+void make_up_roots(int W, int U, float2* out);
+cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
+                              const float2* tw, cudaStream_t s);
+cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, int M,
+                              int npatch, const float2* tw, float* cval, int* cidx,
+                              cudaStream_t s);
+cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
+                         int npatch, const float* cval, const int* cidx, const float2* roots,
+                         float* shift, float* gap, cudaStream_t s);
+cudaError_t launch_adam(float* pos, float* m, float* v, const float* g, int N, float lr,
+                        float b1, float b2, float eps, float bc1, float bc2, float max_step,
+                        float ymax, float xmax, cudaStream_t s);
+
 cudaError_t launch_fft2(void* data, int W, int batch, int inverse,
                         const float2* tw, cudaStream_t s);
 cudaError_t launch_finite_check(const float* p, size_t n, int* flag,

@@ -1,0 +1,422 @@
+// XCORR_A registration and the Adam position step (Adam-based position
+// refinement section of Guzzi et al., arXiv 2205.04295; Eqs. 8-9,
+// Algorithm 1; registration after Guizar-Sicairos, Thurman & Fienup,
+// Opt. Lett. 33, 156, 2008).
+//
+// For each patch of a group, after pass C, the scratch holds
+//   plane M     : A = F(o_j)            (crop before the update; passes A, B)
+//   plane M + 1 : row DFTs of o'_j      (refined crop; pass C)
+// xcorr_cols : column DFTs of plane M+1 -> B = F(o'_j); X = B conj(A) is stored
+//              in plane M; inverse column DFTs of X into plane M+1.
+// xcorr_rows : inverse row DFTs of plane M+1 -> c = F^-1 X (unnormalised);
+//              per row block the largest |c|^2 and its first row-major index.
+// updft      : coarse peak (s_y, s_x) wrapped to [-W/2, W/2); the
+//              cross-correlation re-evaluated on the K x K grid
+//              s + (k - K/2)/U as E_r X E_c; its first maximum gives the
+//              shift s_j; the stored measurement is g_j = -s_j.
+// adam       : one Adam step per position with g_j as the gradient, then the
+//              position is clamped so that its crop stays inside the object.
+//
+// The phase of every matrix-DFT entry is an exact integer multiple of
+// 2 pi / (U W): entry (v, k) of E_c is root[(v_s (U s_x + k - K/2)) mod (U W)]
+// with v_s the signed frequency; the roots come from a host table.
+#include "pty_fft.cuh"
+#include "pty_internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace pty {
+
+namespace {
+
+// larger value wins; equal values: smaller index wins (first in row-major order)
+PTY_D void best_merge(float& v, int& i, float v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+PTY_D void warp_best(float& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    best_merge(v, i, v2, i2);
+  }
+}
+
+// Block-wide best (value, index); every thread gets it.  Contains barriers.
+PTY_D void block_best(float& v, int& i, float* rv, int* ri) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  warp_best(v, i);
+  __syncthreads();
+  if (l == 0) {
+    rv[w] = v;
+    ri[w] = i;
+  }
+  __syncthreads();
+  v = rv[0];
+  i = ri[0];
+  for (int k = 1; k < nw; ++k) best_merge(v, i, rv[k], ri[k]);
+}
+
+PTY_D int wrap_shift(int i, int W) { return i >= W / 2 ? i - W : i; }
+PTY_D int modp(long long a, int m) {
+  long long r = a % m;
+  return (int)(r < 0 ? r + m : r);
+}
+
+// ------------------------------------------------------------ xcorr_cols
+template <int W>
+__global__ void __launch_bounds__(256)
+k_xcorr_cols(float2* __restrict__ scratch, int npl, int M, int CB,
+             const float2* __restrict__ tw_g) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* tbuf = tw + W;
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  const int lp = blockIdx.y, c0 = blockIdx.x * CB;
+  const int c = threadIdx.x % CB, lane = threadIdx.x / CB;
+  const bool act = lane < G::L;
+  float2* colA = scratch + ((size_t)lp * npl + M) * W * W + c0 + c;
+  float2* colB = colA + (size_t)W * W;
+  float2* lbuf = tbuf + c * G::LP;
+  __syncthreads();
+  float2 v[G::N1];
+  if (act && lane < G::N2) {
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = colB[(size_t)(G::N2 * n1 + lane) * W];
+    fwd_step1<W>(v, lane, tw, lbuf);
+  }
+  __syncthreads();
+  float2 z[G::N2];
+  if (act && lane < G::N1) {
+    fwd_step3<W>(z, lane, lbuf);
+#pragma unroll
+    for (int k2 = 0; k2 < G::N2; ++k2) {
+      const size_t u = lane + G::N1 * k2;
+      const float2 X = cmulc(z[k2], colA[u * W]);  // B conj(A)
+      colA[u * W] = X;
+      z[k2] = X;
+    }
+  }
+  __syncthreads();  // all transposes read before they are overwritten
+  if (act && lane < G::N1) inv_stepA<W>(z, lane, tw, lbuf);
+  __syncthreads();
+  if (act && lane < G::N2) {
+    inv_stepB<W>(v, lane, lbuf);
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) colB[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
+  }
+}
+
+// ------------------------------------------------------------ xcorr_rows
+template <int W>
+__global__ void __launch_bounds__(256)
+k_xcorr_rows(const float2* __restrict__ scratch, int npl, int M, int RX,
+             const float2* __restrict__ tw_g, float* __restrict__ cval,
+             int* __restrict__ cidx) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* tbuf = tw + W;
+  __shared__ float rv[32];
+  __shared__ int ri[32];
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  __syncthreads();
+  const int lp = blockIdx.y, r0 = blockIdx.x * RX;
+  const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
+  const bool act = line < RX;
+  float2* lbuf = tbuf + line * G::LP;
+  const float2* row = scratch + (((size_t)lp * npl + M + 1) * W + r0 + (act ? line : 0)) * W;
+  if (act && lane < G::N1) {
+    float2 z[G::N2];
+#pragma unroll
+    for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = row[lane + G::N1 * k2];
+    inv_stepA<W>(z, lane, tw, lbuf);
+  }
+  __syncthreads();
+  float best = -1.f;
+  int bi = 0x7fffffff;
+  if (act && lane < G::N2) {
+    float2 v[G::N1];
+    inv_stepB<W>(v, lane, lbuf);
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1)
+      best_merge(best, bi, cabs2(v[n1]), (r0 + line) * W + G::N2 * n1 + lane);
+  }
+  block_best(best, bi, rv, ri);
+  if (threadIdx.x == 0) {
+    cval[(size_t)lp * gridDim.x + blockIdx.x] = best;
+    cidx[(size_t)lp * gridDim.x + blockIdx.x] = bi;
+  }
+}
+
+// ------------------------------------------------------------ updft
+// One CTA per patch: coarse peak, T = X E_c (W x K, shared memory), then
+// c_up = E_r T (K x K), first maximum -> shift.
+template <int W>
+__global__ void __launch_bounds__(256)
+k_updft(const float2* __restrict__ scratch, int npl, int M, const int* __restrict__ ids,
+        int nparts, const float* __restrict__ cval, const int* __restrict__ cidx,
+        const float2* __restrict__ roots_g, int U, int K, float* __restrict__ shift,
+        float* __restrict__ gap) {
+  extern __shared__ float4 smem4[];
+  const int UW = U * W;
+  float2* roots = reinterpret_cast<float2*>(smem4);
+  float2* T = roots + UW;                // [W][K]
+  float2* xrow = T + (size_t)W * K;      // [8 warps][W]
+  __shared__ float rv[32];
+  __shared__ int ri[32];
+  __shared__ int s_sy, s_sx;
+  const int lp = blockIdx.x, j = ids[lp];
+  for (int e = threadIdx.x; e < UW; e += blockDim.x) roots[e] = roots_g[e];
+  // coarse peak over the row-block partials
+  {
+    float b = -1.f;
+    int bi = 0x7fffffff;
+    for (int e = threadIdx.x; e < nparts; e += blockDim.x)
+      best_merge(b, bi, cval[(size_t)lp * nparts + e], cidx[(size_t)lp * nparts + e]);
+    block_best(b, bi, rv, ri);
+    if (threadIdx.x == 0) {
+      s_sy = wrap_shift(bi / W, W);
+      s_sx = wrap_shift(bi % W, W);
+    }
+  }
+  __syncthreads();
+  const int sy = s_sy, sx = s_sx, half = K / 2;
+  const float2* X = scratch + ((size_t)lp * npl + M) * W * W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarp = blockDim.x >> 5;
+  float2* xr = xrow + warp * W;
+  // T[u][k] = sum_v X[u][v] root[(v_s (U sx + k - half)) mod UW]
+  for (int u = warp; u < W; u += nwarp) {
+    for (int v = lane; v < W; v += 32) xr[v] = X[(size_t)u * W + v];
+    __syncwarp();
+    for (int k = lane; k < K; k += 32) {
+      const int a = modp((long long)U * sx + k - half, UW);
+      float2 acc = make_float2(0.f, 0.f);
+      int n = 0;  // (v * a) mod UW for v = 0, 1, ..
+      for (int v = 0; v < W / 2; ++v) {
+        acc = cadd(acc, cmul(xr[v], roots[n]));
+        n += a;
+        if (n >= UW) n -= UW;
+      }
+      n = modp(-(long long)(W / 2) * a, UW);  // v_s = v - W from v = W/2
+      for (int v = W / 2; v < W; ++v) {
+        acc = cadd(acc, cmul(xr[v], roots[n]));
+        n += a;
+        if (n >= UW) n -= UW;
+      }
+      T[(size_t)u * K + k] = acc;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // c_up[k1][k2] = sum_u root[(u_s (U sy + k1 - half)) mod UW] T[u][k2]
+  float best = -1.f, second = -1.f;
+  int bi = 0x7fffffff;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int k1 = e / K, k2 = e - k1 * K;
+    const int b = modp((long long)U * sy + k1 - half, UW);
+    float2 acc = make_float2(0.f, 0.f);
+    int n = 0;
+    for (int u = 0; u < W / 2; ++u) {
+      acc = cadd(acc, cmul(roots[n], T[(size_t)u * K + k2]));
+      n += b;
+      if (n >= UW) n -= UW;
+    }
+    n = modp(-(long long)(W / 2) * b, UW);
+    for (int u = W / 2; u < W; ++u) {
+      acc = cadd(acc, cmul(roots[n], T[(size_t)u * K + k2]));
+      n += b;
+      if (n >= UW) n -= UW;
+    }
+    const float m = cabs2(acc);
+    if (m > best || (m == best && e < bi)) {
+      second = fmaxf(second, best);
+      best = m;
+      bi = e;
+    } else {
+      second = fmaxf(second, m);
+    }
+  }
+  // global best, then the best value among all other grid points
+  float gb = best;
+  int gbi = bi;
+  block_best(gb, gbi, rv, ri);
+  float s2 = (bi == gbi) ? second : best;  // this thread's best that is not the winner
+  __syncthreads();
+  {
+    int dummy = 0;
+    block_best(s2, dummy, rv, ri);
+  }
+  if (threadIdx.x == 0) {
+    const int k1 = gbi / K, k2 = gbi % K;
+    const float y = (float)sy + (float)(k1 - half) / (float)U;
+    const float x = (float)sx + (float)(k2 - half) / (float)U;
+    shift[2 * j] = -y;
+    shift[2 * j + 1] = -x;
+    gap[j] = gb > 0.f ? (gb - fmaxf(s2, 0.f)) / gb : 0.f;
+  }
+}
+
+// U <= 1: the coarse peak alone.
+__global__ void k_coarse_only(const int* __restrict__ ids, int nparts, int W,
+                              const float* __restrict__ cval, const int* __restrict__ cidx,
+                              float* __restrict__ shift, float* __restrict__ gap) {
+  __shared__ float rv[32];
+  __shared__ int ri[32];
+  const int lp = blockIdx.x, j = ids[lp];
+  float b = -1.f;
+  int bi = 0x7fffffff;
+  for (int e = threadIdx.x; e < nparts; e += blockDim.x)
+    best_merge(b, bi, cval[(size_t)lp * nparts + e], cidx[(size_t)lp * nparts + e]);
+  block_best(b, bi, rv, ri);
+  if (threadIdx.x == 0) {
+    shift[2 * j] = -(float)wrap_shift(bi / W, W);
+    shift[2 * j + 1] = -(float)wrap_shift(bi % W, W);
+    gap[j] = 1.f;
+  }
+}
+
+// ------------------------------------------------------------ adam
+__global__ void k_adam(float* __restrict__ pos, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, int N, float lr, float b1, float b2,
+                       float eps, float bc1, float bc2, float max_step, float ymax,
+                       float xmax) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * N) return;
+  const float gi = g[i];
+  const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+  const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+  m[i] = mi;
+  v[i] = vi;
+  float step = lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  if (max_step > 0.f) step = fminf(fmaxf(step, -max_step), max_step);
+  const float hi = (i & 1) ? xmax : ymax;
+  pos[i] = fminf(fmaxf(pos[i] + step, 0.f), hi);
+}
+
+int pow2_floor(int v) {
+  int p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+
+}  // namespace
+
+#define PTY_DISPATCH_W(W, ...)                                 \
+  switch (W) {                                                 \
+    case 32: { constexpr int WW = 32; __VA_ARGS__; } break;     \
+    case 64: { constexpr int WW = 64; __VA_ARGS__; } break;     \
+    case 96: { constexpr int WW = 96; __VA_ARGS__; } break;     \
+    case 128: { constexpr int WW = 128; __VA_ARGS__; } break;   \
+    case 192: { constexpr int WW = 192; __VA_ARGS__; } break;   \
+    case 256: { constexpr int WW = 256; __VA_ARGS__; } break;   \
+    default: return cudaErrorInvalidValue;                     \
+  }
+
+template <int W> static void refgeo_fill(RefGeo& g) {
+  using G = Line<W>;
+  g.CBX = std::min(16, pow2_floor(256 / G::L));
+  while ((W / 2) % g.CBX) g.CBX /= 2;
+  g.RX = std::min(W, pow2_floor(256 / G::L));
+  while (W % g.RX) g.RX /= 2;
+  g.smX = (size_t)(W + g.CBX * G::LP) * sizeof(float2);
+  g.smR = (size_t)(W + g.RX * G::LP) * sizeof(float2);
+}
+
+RefGeo make_refgeo(int W, int U) {
+  RefGeo g{};
+  g.W = W;
+  g.U = std::max(1, U);
+  g.K = (int)std::ceil(1.5 * g.U);
+  switch (W) {
+    case 32: refgeo_fill<32>(g); break;
+    case 64: refgeo_fill<64>(g); break;
+    case 96: refgeo_fill<96>(g); break;
+    case 128: refgeo_fill<128>(g); break;
+    case 192: refgeo_fill<192>(g); break;
+    default: refgeo_fill<256>(g); break;
+  }
+  g.smU = (size_t)(g.U * W + (size_t)W * g.K + 8 * W) * sizeof(float2);
+  return g;
+}
+
+cudaError_t set_refine_smem(const RefGeo& g) {
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(g.W, {
+    e = cudaFuncSetAttribute(k_xcorr_cols<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)g.smX);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_xcorr_rows<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)g.smR);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_updft<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)g.smU);
+  });
+  return e;
+}
+
+void make_up_roots(int W, int U, float2* out) {
+  const double pi = 3.14159265358979323846;
+  const int n = U * W;
+  for (int m = 0; m < n; ++m) {
+    const double th = 2.0 * pi * (double)m / (double)n;
+    out[m] = make_float2((float)std::cos(th), (float)std::sin(th));
+  }
+}
+
+cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
+                              const float2* tw, cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  PTY_DISPATCH_W(g.W, {
+    using G = Line<WW>;
+    k_xcorr_cols<WW><<<dim3(WW / g.CBX, npatch), g.CBX * G::L, g.smX, s>>>(scratch, npl, M,
+                                                                           g.CBX, tw);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, int M,
+                              int npatch, const float2* tw, float* cval, int* cidx,
+                              cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  PTY_DISPATCH_W(g.W, {
+    using G = Line<WW>;
+    const int thr = (g.RX * G::L + 31) / 32 * 32;
+    k_xcorr_rows<WW><<<dim3(WW / g.RX, npatch), thr, g.smR, s>>>(scratch, npl, M, g.RX, tw,
+                                                                 cval, cidx);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
+                         int npatch, const float* cval, const int* cidx, const float2* roots,
+                         float* shift, float* gap, cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  const int nparts = g.W / g.RX;
+  if (g.U <= 1) {
+    k_coarse_only<<<npatch, 128, 0, s>>>(ids, nparts, g.W, cval, cidx, shift, gap);
+    return cudaGetLastError();
+  }
+  PTY_DISPATCH_W(g.W, (k_updft<WW><<<npatch, 256, g.smU, s>>>(scratch, npl, M, ids, nparts,
+                                                              cval, cidx, roots, g.U, g.K,
+                                                              shift, gap)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* pos, float* m, float* v, const float* g, int N, float lr,
+                        float b1, float b2, float eps, float bc1, float bc2, float max_step,
+                        float ymax, float xmax, cudaStream_t s) {
+  const int n = 2 * N;
+  k_adam<<<(n + 255) / 256, 256, 0, s>>>(pos, m, v, g, N, lr, b1, b2, eps, bc1, bc2, max_step,
+                                         ymax, xmax);
+  return cudaGetLastError();
+}
+
+}  // namespace pty

@@ -68,7 +68,7 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
            int M, int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
            const float2* __restrict__ tw_g, float2* __restrict__ scratch,
-           float* __restrict__ omax_part) {
+           float* __restrict__ omax_part, int npl, int xo) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
@@ -85,8 +85,9 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
   }
   __syncthreads();
 
+  // lines: (mode k, row r) for k < M, and with xo the crop itself as plane M
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
-  const bool act = line < M * R;
+  const bool act = line < (M + xo) * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
   const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
@@ -102,7 +103,7 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
         const float2 o = __ldg(orow + c);
-        v[n1] = cmul(prow[c], o);
+        v[n1] = k < M ? cmul(prow[c], o) : o;
         omax = fmaxf(omax, cabs2(o));
       }
       fwd_step1<W>(v, lane, tw, lbuf);
@@ -111,7 +112,7 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
     if (act && lane < G::N1) {
       float2 z[G::N2];
       fwd_step3<W>(z, lane, lbuf);
-      float2* dst = scratch + (((size_t)lp * M + k) * W + r0 + r) * W;
+      float2* dst = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
     }
@@ -126,21 +127,23 @@ __global__ void __launch_bounds__(512)
 k_cols(float2* __restrict__ scratch, int M, int CB,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part) {
+       float* __restrict__ err_part, int npl, int xo) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* tbuf = tw + W;
-  float* Sb = reinterpret_cast<float*>(tbuf + M * CB * G::LP);
+  float* Sb = reinterpret_cast<float*>(tbuf + (M + xo) * CB * G::LP);
   __shared__ float red[32];
 
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   const int lp = blockIdx.y, c0 = blockIdx.x * CB;
   const int c = threadIdx.x % CB, rest = threadIdx.x / CB;
   const int lane = rest % G::L, k = rest / G::L;
-  const bool act = k < M;
+  // k < M: the modes; k == M (with xo): the crop, forward transform only
+  const bool act = k < M + xo;
+  const bool mode = k < M;
   const int j = ids[lp];
-  float2* col = scratch + ((size_t)lp * M + (act ? k : 0)) * W * W + c0 + c;
+  float2* col = scratch + ((size_t)lp * npl + (act ? k : 0)) * W * W + c0 + c;
   float2* lbuf = tbuf + ((act ? k : 0) * CB + c) * G::LP;
   __syncthreads();
 
@@ -154,13 +157,18 @@ k_cols(float2* __restrict__ scratch, int M, int CB,
   float2 z[G::N2];
   if (act && lane < G::N1) {
     fwd_step3<W>(z, lane, lbuf);
+    if (mode) {
 #pragma unroll
-    for (int k2 = 0; k2 < G::N2; ++k2)
-      Sb[(k * CB + c) * W + lane + G::N1 * k2] = cabs2(z[k2]);
+      for (int k2 = 0; k2 < G::N2; ++k2)
+        Sb[(k * CB + c) * W + lane + G::N1 * k2] = cabs2(z[k2]);
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2) col[(size_t)(lane + G::N1 * k2) * W] = z[k2];
+    }
   }
   __syncthreads();
   float e = 0.f;
-  if (act && lane < G::N1) {
+  if (mode && lane < G::N1) {
     const int iv = (c0 + c + W / 2) % W;
     const uint16_t* Ij = I + (size_t)j * W * W + iv;
     const float f2 = inv_w * inv_w;
@@ -181,7 +189,7 @@ k_cols(float2* __restrict__ scratch, int M, int CB,
     inv_stepA<W>(z, lane, tw, lbuf);
   }
   __syncthreads();
-  if (act && lane < G::N2) {
+  if (mode && lane < G::N2) {
     inv_stepB<W>(v, lane, lbuf);
 #pragma unroll
     for (int n1 = 0; n1 < G::N1; ++n1) col[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
@@ -196,11 +204,11 @@ __global__ void __launch_bounds__(256)
 k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
            int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
-           const float2* __restrict__ scratch, const float* __restrict__ omax_part,
+           float2* __restrict__ scratch, const float* __restrict__ omax_part,
            const float* __restrict__ pmax_part, int n_pmax,
            const float2* __restrict__ tw_g, UpdArgs a,
            float2* __restrict__ pnum, float* __restrict__ pden,
-           float* __restrict__ osum, int accumulate) {
+           float* __restrict__ osum, int accumulate, int npl, int refine) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   const int TB = max(M * R * G::LP, M * R * W);
@@ -208,7 +216,8 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
   float2* Prow = tw + W;
   float2* tbuf = Prow + M * R * W;  // transpose buffer, then D conj(P) terms
   float2* num = tbuf + TB;
-  float* Pint = reinterpret_cast<float*>(num + M * R * W);
+  float2* onew = num + M * R * W;   // refined crop rows (refine only)
+  float* Pint = reinterpret_cast<float*>(onew + (refine ? R * W : 0));
   float* den = Pint + R * W;
   __shared__ float s_pmax, s_omax;
 
@@ -252,7 +261,7 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
       if (threadIdx.x == 0) s_omax = m;
     }
     if (act && lane < G::N1) {
-      const float2* src = scratch + (((size_t)lp * M + k) * W + r0 + r) * W;
+      const float2* src = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
       float2 z[G::N2];
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
@@ -287,11 +296,31 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
       for (int kk = 0; kk < M; ++kk) s = cadd(s, tbuf[(kk * R + rr) * W + c]);
       const float dn = fmaf(1.f - a.gamma, Pint[e], gden);
       const float sc = dn > 0.f ? a.alpha_O / dn : 0.f;  // zero numerator too
-      *op = make_float2(fmaf(sc, s.x, o.x), fmaf(sc, s.y, o.y));
+      const float2 on = make_float2(fmaf(sc, s.x, o.x), fmaf(sc, s.y, o.y));
+      *op = on;
+      if (refine) onew[e] = on;
       den[e] += fmaf(1.f - a.beta, cabs2(o), a.beta * om);
     }
     osum_local += om;
     __syncthreads();
+    if (refine) {
+      // forward row DFTs of the refined crop o'_j -> plane M + 1 (XCORR_A)
+      if (line < R && lane < G::N2) {
+        float2 v2[G::N1];
+#pragma unroll
+        for (int n1 = 0; n1 < G::N1; ++n1) v2[n1] = onew[line * W + G::N2 * n1 + lane];
+        fwd_step1<W>(v2, lane, tw, tbuf + line * G::LP);
+      }
+      __syncthreads();
+      if (line < R && lane < G::N1) {
+        float2 z[G::N2];
+        fwd_step3<W>(z, lane, tbuf + line * G::LP);
+        float2* dst = scratch + (((size_t)lp * npl + M + 1) * W + r0 + line) * W;
+#pragma unroll
+        for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
+      }
+      __syncthreads();
+    }
   }
   const int slot = blockIdx.y;
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
@@ -536,10 +565,13 @@ bool supported_W(int W) {
     default: return cudaErrorInvalidValue;                   \
   }
 
-Tiling make_tiling(int W, int M) {
+Tiling make_tiling(int W, int M, bool refine) {
   Tiling t{};
   t.W = W;
   t.M = M;
+  t.xo = refine ? 1 : 0;
+  t.refine = refine ? 1 : 0;
+  t.npl = refine ? M + 2 : M;
   int L = 16, LP = W;
   switch (W) {
     case 32: geo<32>(L, LP); break;
@@ -549,23 +581,24 @@ Tiling make_tiling(int W, int M) {
     case 192: geo<192>(L, LP); break;
     default: geo<256>(L, LP); break;
   }
-  int R = pow2_floor(std::max(1, 256 / (M * L)));
+  const int MA = M + t.xo;  // lines per row in pass A, columns-groups in pass B
+  int R = pow2_floor(std::max(1, 256 / (MA * L)));
   R = std::min(R, 16);
   while (W % R) R /= 2;
   t.R = R;
   t.ppc = 4;
-  int CB = pow2_floor(std::max(1, 512 / (M * L)));
-  CB = std::max(2, std::min(16, CB));  // M * CB * L <= 512 threads
+  int CB = pow2_floor(std::max(1, 512 / (MA * L)));
+  CB = std::max(2, std::min(16, CB));  // MA * CB * L <= 512 threads
   while ((W / 2) % CB) CB /= 2;
   t.CB = CB;
-  t.thrA = round32(M * R * L);
-  t.thrC = t.thrA;
-  t.thrB = round32(M * CB * L);
-  t.smA = (size_t)(W + M * R * W + M * R * LP) * sizeof(float2);
-  t.smB = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
-  t.smI = t.smB;
+  t.thrA = round32(MA * R * L);
+  t.thrC = round32(M * R * L);
+  t.thrB = round32(MA * CB * L);
+  t.smA = (size_t)(W + M * R * W + MA * R * LP) * sizeof(float2);
+  t.smB = (size_t)(W + MA * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
+  t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
-  t.smC = (size_t)(W + M * R * W + TB + M * R * W) * sizeof(float2) +
+  t.smC = (size_t)(W + M * R * W + TB + M * R * W + (refine ? R * W : 0)) * sizeof(float2) +
           (size_t)2 * R * W * sizeof(float);
   t.n_pmax = std::max(1, std::min(64, W * W / 1024));
   return t;
@@ -601,7 +634,21 @@ cudaError_t launch_rows_fwd(const Tiling& t, const float2* O, int Hx, const floa
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
   PTY_DISPATCH_W(t.W, (k_rows_fwd<WW><<<grid, t.thrA, t.smA, s>>>(
                           O, Hx, P, t.M, t.R, t.ppc, ids, corners, npatch, tw,
-                          scratch, omax_part)));
+                          scratch, omax_part, t.npl, t.xo)));
+  return cudaGetLastError();
+}
+
+// Pass A with the plain layout (M planes, no crop plane) whatever t says:
+// used by the model-intensity computation.
+cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx, const float2* P,
+                                  const int* ids, const int2* corners, int npatch,
+                                  const float2* tw, float2* scratch, float* omax_part,
+                                  cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
+  PTY_DISPATCH_W(t.W, (k_rows_fwd<WW><<<grid, t.thrA, t.smA, s>>>(
+                          O, Hx, P, t.M, t.R, t.ppc, ids, corners, npatch, tw,
+                          scratch, omax_part, t.M, 0)));
   return cudaGetLastError();
 }
 
@@ -611,13 +658,13 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, npatch);
   PTY_DISPATCH_W(t.W, (k_cols<WW><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, t.CB, I, ids, tw, inv_w, eps, err_part)));
+                          scratch, t.M, t.CB, I, ids, tw, inv_w, eps, err_part, t.npl, t.xo)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             const int* ids, const int2* corners, int npatch,
-                            const float2* scratch, const float* omax_part,
+                            float2* scratch, const float* omax_part,
                             const float* pmax_part, const float2* tw,
                             const UpdArgs& a, float2* pnum, float* pden,
                             float* osum, int accumulate, cudaStream_t s) {
@@ -626,7 +673,7 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
   PTY_DISPATCH_W(t.W, (k_rows_inv<WW><<<grid, t.thrC, t.smC, s>>>(
                           O, Hx, P, t.M, t.R, t.ppc, ids, corners, npatch, scratch,
                           omax_part, pmax_part, t.n_pmax, tw, a, pnum, pden, osum,
-                          accumulate)));
+                          accumulate, t.npl, t.refine)));
   return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ _SIGS = {
                                     c_int_p]),
     "pty_fft2": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
     "pty_profile": (c_int, [c_void_p, c_int]),
+    "pty_get_refine_gaps": (c_int, [c_void_p, c_void_p, c_int]),
     "pty_model_intensities_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int,
                                               c_void_p, c_int, c_void_p, c_void_p]),
     "pty_get_stats": (c_int, [c_void_p, ctypes.POINTER(Stats), c_int]),
@@ -274,6 +275,9 @@ class Problem:
 
     def positions(self, device=True):
         return self._get(lib().pty_get_positions, (self.N, 2), _dt("f32"), device)
+
+    def refine_gaps(self, device=False):
+        return self._get(lib().pty_get_refine_gaps, (self.N,), _dt("f32"), device)
 
     def model_intensities(self, device=True):
         return self._get(lib().pty_model_intensities, (self.N, self.W, self.W), _dt("f32"), device)

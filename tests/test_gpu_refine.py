@@ -1,0 +1,163 @@
+"""Parity of XCORR_A registration + Adam position refinement (CUDA) with the
+FP64 oracle.
+
+The registration ends in an argmax over a 1/U-pixel grid; both sides take
+it in float32 (see oracle.registration), and measured shifts must then agree
+exactly except where the two best grid values are within NEAR_TIE of each
+other on either side: such flips are counted and must all be near-ties.
+Long runs are checked in lock-step: every iteration starts the GPU from the
+oracle's state (object, probe, positions, Adam moments) and the single-
+iteration transition is compared, so registration error is separated from
+the drift that one flipped argmax causes in a free run.  Bars: positions
+within 0.01 px, object and probe relative L2 <= 1e-5 per transition."""
+import numpy as np
+import pytest
+
+from helpers import build, rel_l2
+from oracle import rpie
+from paper_2205_04295_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+NEAR_TIE = 1e-5
+
+
+def pair(wl, d, lr=0.5, U=20, start=0, **kw):
+    from paper_2205_04295_b300 import pty
+    prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
+    prob.set_data(d["I"], d["pos"], d["O0"], d["P0"])
+    st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+    pg, po = pty.rpie_params(**kw), rpie.RPIEParams(**kw)
+    rg = pty.refine_params(upsample=U, lr=lr, start_iter=start)
+    ro = rpie.RefineParams(upsample=U, lr=lr, start_iter=start)
+    return prob, st, pg, po, rg, ro
+
+
+def step_both(prob, st, d, pg, po, rg, ro):
+    eg, sh = prob.refine(1, pg, rg, shifts=True)
+    eo = rpie.iterate(st, d["I"], po, ro)
+    return eg[0], eo, sh, prob.refine_gaps()
+
+
+def compare_step(prob, st, sh, gaps):
+    """Returns the mask of flipped shifts after checking they are near-ties."""
+    flip = np.abs(sh - st.last_shift).max(1) > 1e-5
+    tie = (gaps <= NEAR_TIE) | (st.gap <= NEAR_TIE)
+    assert not np.any(flip & ~tie), "shift differs at a clear maximum: %s" % np.nonzero(flip & ~tie)
+    pos = prob.positions(False)
+    d = np.abs(pos - st.pos).max(1)
+    assert np.all(d[~flip] <= 0.01), d[~flip].max()
+    return flip
+
+
+def load_state(prob, st):
+    prob.set_object(st.O.astype(np.complex64))
+    prob.set_probe(st.P.astype(np.complex64))
+    prob.set_positions(st.pos.astype(np.float32))
+    prob.set_adam_state(st.m.astype(np.float32), st.v.astype(np.float32), st.t, st.it)
+
+
+def test_one_iteration_shifts_positions_object_probe():
+    wl = synth.tiny(W=64, M=2, ny=5, nx=5, step=10.0, seed=31, photons=1e6, jitter=1.5, err=2.0)
+    d = build(wl)
+    prob, st, pg, po, rg, ro = pair(wl, d)
+    eg, eo, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+    flip = compare_step(prob, st, sh, gaps)
+    assert flip.sum() <= 2
+    assert rel_l2(prob.object(False), st.O) <= 1e-5
+    assert rel_l2(prob.probe(False), st.P) <= 1e-5
+    assert abs(eg - eo) <= 1e-5 * eo
+
+
+def test_start_iter_and_lockstep_256():
+    wl = synth.tiny(W=256, M=5, ny=2, nx=3, step=48.0, seed=32, photons=1e6, jitter=1.0, err=1.5)
+    d = build(wl)
+    prob, st, pg, po, rg, ro = pair(wl, d, start=1)
+    step_both(prob, st, d, pg, po, rg, ro)                     # plain iteration
+    np.testing.assert_array_equal(prob.positions(False), d["pos"])
+    for _ in range(3):
+        load_state(prob, st)
+        _, _, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+        compare_step(prob, st, sh, gaps)
+        assert rel_l2(prob.object(False), st.O) <= 1e-5
+        assert rel_l2(prob.probe(False), st.P) <= 1e-5
+    m, v, t, it = prob.adam_state()
+    assert t == 3 and it == 4 and st.t == 3
+
+
+def test_coarse_only_registration():
+    wl = synth.tiny(W=32, M=1, ny=4, nx=4, step=6.0, seed=33, jitter=1.0, err=2.0)
+    d = build(wl)
+    prob, st, pg, po, rg, ro = pair(wl, d, U=1, start=1)
+    step_both(prob, st, d, pg, po, rg, ro)
+    load_state(prob, st)
+    eg, eo, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+    np.testing.assert_allclose(sh, st.last_shift, atol=1e-6)
+
+
+def subset_128(ny=5, nx=5):
+    full = synth.refine_128()
+    sel = (np.arange(40)[:ny, None] * 40 + np.arange(nx)[None, :]).ravel()
+    wl = synth.refine_128()
+    wl.pos, wl.pos_true = full.pos[sel], full.pos_true[sel]
+    lo = np.floor(wl.pos_true.min(0)) - 8
+    wl.pos_true = wl.pos_true - lo
+    wl.pos = np.clip(wl.pos - lo, 0, None).astype(np.float32)
+    wl.Hy = wl.Hx = int(np.ceil(max(wl.pos_true.max(), wl.pos.max()))) + 128 + 8
+    return wl
+
+
+def test_refine_128_modes3_100_iterations_lockstep():
+    """128x128 patterns, 3 modes, the first 5x5 block of the jittered 40x40
+    raster with its +-3 px supplied error, U = 20, lr 0.5: 100 iterations,
+    refinement from iteration 10, every transition compared."""
+    wl = subset_128()
+    d = build(wl)
+    prob, st, pg, po, rg, ro = pair(wl, d, start=10)
+    flips = 0
+    for it in range(100):
+        load_state(prob, st)
+        eg, eo, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+        if it >= 10:
+            flips += compare_step(prob, st, sh, gaps).sum()
+        assert rel_l2(prob.object(False), st.O) <= 1e-5
+        assert rel_l2(prob.probe(False), st.P) <= 1e-5
+        assert abs(eg - eo) <= 1e-4 * eo
+    assert flips <= 0.05 * 90 * wl.N
+
+
+def test_refine_128_free_run_tracks_oracle():
+    """The same subset run freely for 30 iterations (refinement from 10).
+    Until the first near-tie argmax flips, the runs agree to 1e-5 in object
+    and to 0.01 px in position; after it, one shift differs by 1/U and the
+    trajectories separate, so only the error curve is compared (10 %)."""
+    wl = subset_128()
+    d = build(wl)
+    prob, st, pg, po, rg, ro = pair(wl, d, start=10)
+    eg, eo = [], []
+    first_flip = None
+    for it in range(30):
+        a, b, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+        eg.append(a)
+        eo.append(b)
+        if first_flip is None:
+            flip = compare_step(prob, st, sh, gaps) if it >= 10 else np.zeros(wl.N, bool)
+            if flip.any():
+                first_flip = it
+            else:
+                assert rel_l2(prob.object(False), st.O) <= 1e-5
+                assert abs(a - b) <= 1e-4 * b
+    np.testing.assert_allclose(eg, eo, rtol=0.1)
+
+
+def test_full_size_refine_128_one_iteration():
+    """The full 128x128 / 3-mode / 1600-position scan, one refining iteration
+    (one Adam step) in the benchmark's launch configuration."""
+    wl = synth.refine_128()
+    d = build(wl)
+    prob, st, pg, po, rg, ro = pair(wl, d)
+    eg, eo, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+    flip = compare_step(prob, st, sh, gaps)
+    assert flip.mean() <= 0.05
+    assert rel_l2(prob.object(False), st.O) <= 1e-5
+    assert rel_l2(prob.probe(False), st.P) <= 1e-5

@@ -23,23 +23,28 @@ def shifted(a, d):
     return np.fft.ifft2(np.fft.fft2(a) * ph)
 
 
+DT = [np.complex64, np.complex128]
+
+
+@pytest.mark.parametrize("dt", DT)
 @pytest.mark.parametrize("d", [(3.0, -5.0), (0.0, 0.0), (-7.0, 11.0), (31.0, -32.0)])
-def test_integer_shifts_exact(d):
+def test_integer_shifts_exact(d, dt):
     rng = np.random.default_rng(1)
     a = smooth_patch(64, rng)
-    s, _ = registration.xcorr_peak(a, shifted(a, np.array(d)), 20)
+    s, _ = registration.xcorr_peak(a, shifted(a, np.array(d)), 20, dt)
     # equal modulo the patch size; the coarse peak lies in [-W/2, W/2)
     np.testing.assert_allclose(np.mod(s + np.array(d), 64), 0.0, atol=1e-12)
     assert np.all((s >= -32) & (s < 32))
 
 
+@pytest.mark.parametrize("dt", DT)
 @pytest.mark.parametrize("k", [(1, 3), (-7, 13), (19, -19), (-31, 2)])
-def test_grid_subpixel_shifts_exact(k):
+def test_grid_subpixel_shifts_exact(k, dt):
     U = 20
     rng = np.random.default_rng(2)
     a = smooth_patch(64, rng)
     d = np.array([2 + k[0] / U, -1 + k[1] / U])
-    s, _ = registration.xcorr_peak(a, shifted(a, d), U)
+    s, _ = registration.xcorr_peak(a, shifted(a, d), U, dt)
     np.testing.assert_allclose(s, -d, atol=1e-9)
 
 
@@ -68,7 +73,7 @@ def test_matches_zero_padded_brute_force():
         c = np.abs(np.fft.ifft2(big)) ** 2
         n = np.unravel_index(np.argmax(c), c.shape)
         want = np.array([registration.wrap(n[0], U * W), registration.wrap(n[1], U * W)]) / U
-        s, _ = registration.xcorr_peak(a, b, U)
+        s, _ = registration.xcorr_peak(a, b, U, np.complex128)
         np.testing.assert_allclose(s, want, atol=1e-12)
 
 
