@@ -279,6 +279,20 @@ def run_ours(args, wl, rank, world, local):
     flops, bytes_ = algorithmic(wl.W, wl.M)
     hbm = measured_peaks().get("hbm_gbs", 6400.0)
 
+    # ---- gradient step: loss + dL/dO, dL/dP, dL/dpos (fused adjoint)
+    O_t = torch.from_numpy(d["O_true"]).to(dev)
+    for _ in range(max(1, args.warmup)):
+        prob.loss_grad(O_t, P0_dev, pos_dev)
+    gsteps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    barrier(world)
+    start.record(stream)
+    for _ in range(gsteps):
+        prob.loss_grad(O_t, P0_dev, pos_dev)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    grad_ms = max_over_ranks(start.elapsed_time(stop) / gsteps, world)
+
     # ---- end to end through the C ABI with pinned host buffers
     I_h = I_dev.to(torch.int32).cpu().to(torch.uint16).pin_memory() if hasattr(torch, "uint16") else None
     pos_h = pos_dev.cpu().pin_memory()
@@ -318,6 +332,8 @@ def run_ours(args, wl, rank, world, local):
            "kernel_ms": {k: kst["ms"][k] for k in kinds},
            "kernel_launches": {k: kst["launches"][k] for k in kinds},
            "gpu_launches": launches,
+           "grad": {"ms_per_step": grad_ms, "unit": "ms",
+                    "what": "loss and dL/dO, dL/dP, dL/dpos over all positions, bilinear crops"},
            "e2e": {"value": world * wl.N * e2e_steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "clocks": clk.summary()}

@@ -177,6 +177,23 @@ typedef struct {
 int pty_profile(pty_handle* h, int mode);
 int pty_get_stats(pty_handle* h, pty_stats* out, int reset);
 
+/* Differentiable forward model (bilinear crop at the exact float position,
+ * Eqs. 1, 2, 4) with the amplitude loss
+ *   L = sum_j sum_u (sqrt(sum_p |F(P_p o_j)|^2 + delta) - sqrt(I_j))^2
+ * (delta >= 0 smooths the amplitude where the model is dark; 0 = plain).
+ * O (Hy x Hx complex64), P (M x W x W complex64), pos (N x 2 float) and all
+ * outputs are DEVICE pointers; the handle supplies the data I and scratch.
+ * Every bilinear crop needs floor(pos) >= 0 and floor(pos) + W + 1 <= H
+ * (else PTY_EDATA).  *loss is written on the device (one float).
+ * pty_loss_grad also writes dL/dO (Hy x Hx), dL/dP (M x W x W) as
+ * dL/dRe + i dL/dIm, and dL/dpos (N x 2); the far field is recomputed per
+ * patch rather than stored.  dL/dO is accumulated group by group over
+ * disjoint (W+1)-boxes, so results are bitwise repeatable. */
+int pty_loss(pty_handle* h, const void* O, const void* P, const float* pos,
+             float delta, float* loss);
+int pty_loss_grad(pty_handle* h, const void* O, const void* P, const float* pos,
+                  float delta, float* loss, void* gO, void* gP, float* gpos);
+
 /* Model intensities sum_p |F{P_p o_j}|^2 (Eq. 4) for all j at the current
  * O, P and rounded positions: N*W*W float, detector-centred. */
 int pty_model_intensities(pty_handle* h, float* dst, int mem_kind);

@@ -148,6 +148,12 @@ struct pty_handle {
   int roots_U = 0;
   float *cval = nullptr, *gap = nullptr;
   int* cidx = nullptr;
+  // differentiable form: its own grouping ((W+1)-boxes at floor corners)
+  int Qcg = 1;
+  std::vector<float> gpos_key;
+  std::vector<int> ggptr, ggpos;
+  int* ggpos_d = nullptr;
+  float* gpos_part = nullptr;
   float inv_w = 1.f;
   // device state
   float2 *O = nullptr, *P = nullptr, *tw = nullptr, *scratch = nullptr, *pnum = nullptr;
@@ -418,6 +424,8 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
   h->tlr = pty::make_tiling(h->W, h->M, true);
   if (cudaError_t e = pty::set_smem_limits(h->tl); e != cudaSuccess)
     return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
+  if (cudaError_t e = pty::set_grad_smem(h->tl); e != cudaSuccess)
+    return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
   if (h->tlr.smA > 227 * 1024 || h->tlr.smB > 227 * 1024 || h->tlr.smC > 227 * 1024 ||
       h->tl.smC > 227 * 1024)
     return bail(fail(PTY_EINVAL, "W=%d with M=%d modes exceeds shared memory", h->W, h->M));
@@ -427,10 +435,14 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
   h->Qc = std::min(h->Qc, h->N);
   h->Qcr = (int)std::max<size_t>(1, budget / (W2 * h->tlr.npl * sizeof(float2)));
   h->Qcr = std::min(h->Qcr, h->N);
-  h->nslots = (std::max(h->Qc, h->Qcr) + h->tl.ppc - 1) / h->tl.ppc;
+  h->Qcg = (int)std::max<size_t>(1, budget / (W2 * (h->M + 1) * sizeof(float2)));
+  h->Qcg = std::min(h->Qcg, h->N);
+  h->nslots = (std::max(std::max(h->Qc, h->Qcr), h->Qcg) + h->tl.ppc - 1) / h->tl.ppc;
   h->inv_w = (float)(1.0 / h->W);
   const int nrb = h->W / std::min(h->tl.R, h->tlr.R);
-  const size_t scratch_elems = std::max((size_t)h->Qc * h->tl.npl, (size_t)h->Qcr * h->tlr.npl) * W2;
+  const size_t scratch_elems =
+      std::max(std::max((size_t)h->Qc * h->tl.npl, (size_t)h->Qcr * h->tlr.npl),
+               (size_t)h->Qcg * (h->M + 1)) * W2;
   const size_t nparts = (size_t)h->Qcr * h->W;  // >= Qcr * (W / RX)
   h->err_part_n = (size_t)h->N * (h->W / h->tl.CB);
   int rc = PTY_OK;
@@ -454,6 +466,8 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->shift, (size_t)2 * h->N)) ||
       (rc = alloc_into(h, h->corners, (size_t)h->N)) ||
       (rc = alloc_into(h, h->gpos_d, (size_t)h->N)) ||
+      (rc = alloc_into(h, h->ggpos_d, (size_t)h->N)) ||
+      (rc = alloc_into(h, h->gpos_part, (size_t)h->N * (h->W / h->tl.R) * 2)) ||
       (rc = alloc_into(h, h->iota, (size_t)h->N)) ||
       (rc = alloc_into(h, h->flag, (size_t)4)) ||
       (rc = alloc_into(h, h->sum_d, (size_t)1)))
@@ -627,6 +641,92 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
   }
   CU(cudaStreamSynchronize(h->stream));
   return PTY_OK;
+}
+
+namespace {
+// Validate device positions for the bilinear crop and (re)group them into
+// (W+1)-boxes at floor corners when they changed.
+int grad_prepare(pty_handle* h, const float* pos) {
+  const int N = h->N, W = h->W;
+  std::vector<float> ph(2 * (size_t)N);
+  CU(cudaMemcpyAsync(ph.data(), pos, sizeof(float) * 2 * N, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (ph == h->gpos_key && !h->ggptr.empty()) return PTY_OK;
+  std::vector<int2> c(N);
+  for (int j = 0; j < N; ++j) {
+    const float y = ph[2 * j], x = ph[2 * j + 1];
+    if (!std::isfinite(y) || !std::isfinite(x)) return fail(PTY_EDATA, "position %d is not finite", j);
+    const int iy = (int)std::floor(y), ix = (int)std::floor(x);
+    if (iy < 0 || ix < 0 || iy + W + 1 > h->Hy || ix + W + 1 > h->Hx)
+      return fail(PTY_EDATA, "bilinear crop of position %d leaves the %dx%d object", j, h->Hy, h->Hx);
+    c[j] = make_int2(iy, ix);
+  }
+  greedy_group(c, W + 1, nullptr, 0, h->ggptr, h->ggpos);
+  CU(cudaMemcpyAsync(h->ggpos_d, h->ggpos.data(), sizeof(int) * N, cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->gpos_key = ph;
+  return PTY_OK;
+}
+
+int grad_run(pty_handle* h, const void* Ov, const void* Pv, const float* pos, float delta,
+             float* loss, void* gOv, void* gPv, float* gpos, bool adjoint) {
+  TRY(check_handle(h, true));
+  if (!Ov || !Pv || !pos || !loss) return fail(PTY_EINVAL, "null argument");
+  if (adjoint && (!gOv || !gPv || !gpos)) return fail(PTY_EINVAL, "null gradient output");
+  if (!std::isfinite(delta) || delta < 0.f) return fail(PTY_EINVAL, "delta must be finite and >= 0");
+  TRY(grad_prepare(h, pos));
+  const float2* O = static_cast<const float2*>(Ov);
+  const float2* P = static_cast<const float2*>(Pv);
+  float2* gO = static_cast<float2*>(gOv);
+  const int npl = h->M + 1;
+  const size_t W2 = (size_t)h->W * h->W;
+  if (adjoint) {
+    CU(cudaMemsetAsync(gO, 0, sizeof(float2) * h->Hy * h->Hx, h->stream));
+    CU(cudaMemsetAsync(h->pnum, 0, sizeof(float2) * h->nslots * h->M * W2, h->stream));
+  }
+  CU(cudaMemsetAsync(h->err_part, 0, sizeof(float) * h->err_part_n, h->stream));
+  const int G = (int)h->ggptr.size() - 1;
+  for (int g = 0; g < G; ++g) {
+    const int n = h->ggptr[g + 1] - h->ggptr[g];
+    const int* ids = h->ggpos_d + h->ggptr[g];
+    for (int c0 = 0; c0 < n; c0 += h->Qcg) {
+      const int nc = std::min(h->Qcg, n - c0);
+      const int* idc = ids + c0;
+      pty_handle::Mark m(h, PTY_K_GRAD);
+      CU(pty::launch_grad_rows_fwd(h->tl, O, h->Hx, P, idc, pos, nc, h->tw, h->scratch, npl,
+                                   h->stream));
+      CU(pty::launch_cols_grad(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, delta,
+                               h->err_part, npl, h->stream));
+      h->n_launch[PTY_K_GRAD] += 1;
+      if (adjoint) {
+        CU(pty::launch_grad_rows_inv(h->tl, O, h->Hx, P, idc, pos, nc, h->scratch, npl, h->tw,
+                                     h->pnum, 1, h->gpos_part, h->stream));
+        CU(pty::launch_grad_scatter(h->W, h->M, gO, h->Hx, idc, pos, nc, h->scratch, npl,
+                                    h->stream));
+        h->n_launch[PTY_K_GRAD] += 2;
+      }
+    }
+  }
+  const int used = (std::min(h->Qcg, h->N) + h->tl.ppc - 1) / h->tl.ppc;
+  pty_handle::Mark m(h, PTY_K_GRAD);
+  CU(pty::launch_grad_finish(h->tl, used, h->pnum, adjoint ? static_cast<float2*>(gPv) : nullptr,
+                             h->gpos_part, h->N, adjoint ? gpos : nullptr, h->err_part,
+                             h->err_part_n, loss, h->stream));
+  return PTY_OK;
+}
+}  // namespace
+
+int pty_loss(pty_handle* h, const void* O, const void* P, const float* pos, float delta,
+             float* loss) {
+  g_err.clear();
+  return grad_run(h, O, P, pos, delta, loss, nullptr, nullptr, nullptr, false);
+}
+
+int pty_loss_grad(pty_handle* h, const void* O, const void* P, const float* pos, float delta,
+                  float* loss, void* gO, void* gP, float* gpos) {
+  g_err.clear();
+  return grad_run(h, O, P, pos, delta, loss, gO, gP, gpos, true);
 }
 
 int pty_get_refine_gaps(pty_handle* h, float* dst, int mem_kind) {

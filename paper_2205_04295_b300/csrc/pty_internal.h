@@ -47,6 +47,27 @@ cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx,
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
                         float eps, float* err_part, cudaStream_t s);
+// Fourier-domain step of the gradient (amplitude loss, delta-smoothed).
+cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I,
+                             const int* ids, int npatch, const float2* tw, float inv_w,
+                             float delta, float* loss_part, int npl, cudaStream_t s);
+// ---- differentiable forward model and adjoint (pty_grad.cu) ---------------
+cudaError_t launch_grad_rows_fwd(const Tiling& t, const float2* O, int Hx, const float2* P,
+                                 const int* ids, const float* pos, int npatch,
+                                 const float2* tw, float2* scratch, int npl, cudaStream_t s);
+cudaError_t launch_grad_rows_inv(const Tiling& t, const float2* O, int Hx, const float2* P,
+                                 const int* ids, const float* pos, int npatch,
+                                 float2* scratch, int npl, const float2* tw, float2* gP_part,
+                                 int accumulate, float* gpos_part, cudaStream_t s);
+cudaError_t launch_grad_scatter(int W, int M, float2* gO, int Hx, const int* ids,
+                                const float* pos, int npatch, const float2* scratch, int npl,
+                                cudaStream_t s);
+cudaError_t launch_grad_finish(const Tiling& t, int nslots, const float2* gP_part, float2* gP,
+                               const float* gpos_part, int N, float* gpos,
+                               const float* loss_part, size_t nloss, float* loss,
+                               cudaStream_t s);
+cudaError_t set_grad_smem(const Tiling& t);
+
 cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             const int* ids, const int2* corners, int npatch,
                             float2* scratch, const float* omax_part,

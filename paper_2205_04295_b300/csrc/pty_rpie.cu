@@ -122,7 +122,10 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
 }
 
 // ---------------------------------------------------------------- pass B
-template <int W>
+// GRAD = false: the modulus constraint (Eq. 7).  GRAD = true: the Fourier-
+// domain step of the amplitude-loss adjoint, G_Psi = 2 (1 - sqrt(I) / A) Psi
+// with A = sqrt(S + eps) (eps carries delta), and the loss partial sums.
+template <int W, bool GRAD>
 __global__ void __launch_bounds__(512)
 k_cols(float2* __restrict__ scratch, int M, int CB,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
@@ -160,32 +163,43 @@ k_cols(float2* __restrict__ scratch, int M, int CB,
     if (mode) {
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2)
-        Sb[(k * CB + c) * W + lane + G::N1 * k2] = cabs2(z[k2]);
+        Sb[(k * W + lane + G::N1 * k2) * CB + c] = cabs2(z[k2]);
     } else {
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2) col[(size_t)(lane + G::N1 * k2) * W] = z[k2];
     }
   }
   __syncthreads();
+  // constraint factor once per detector pixel (u, c): S = sum_k |Psi_k|^2 in a
+  // fixed mode order, f = sqrt(I) / (sqrt(S) + eps) folded with both 1/W
+  // normalisations; stored over mode 0's |Psi|^2.
   float e = 0.f;
-  if (mode && lane < G::N1) {
-    const int iv = (c0 + c + W / 2) % W;
-    const uint16_t* Ij = I + (size_t)j * W * W + iv;
+  {
     const float f2 = inv_w * inv_w;
-#pragma unroll
-    for (int k2 = 0; k2 < G::N2; ++k2) {
-      const int u = lane + G::N1 * k2;
+    const uint16_t* Ij = I + (size_t)j * W * W;
+    for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
+      const int u = el / CB, cl = el - u * CB;
       float s = 0.f;
-      for (int kk = 0; kk < M; ++kk) s += Sb[(kk * CB + c) * W + u];
-      const float a = sqrtf(s) * inv_w;
-      const float sI = sqrtf((float)__ldg(Ij + (size_t)((u + W / 2) % W) * W));
-      const float f = sI / (a + eps) * f2;
-      if (k == 0) {
+      for (int kk = 0; kk < M; ++kk) s += Sb[(kk * W + u) * CB + cl];
+      const float sI = sqrtf((float)__ldg(Ij + (size_t)((u + W / 2) % W) * W + (c0 + cl + W / 2) % W));
+      if (!GRAD) {
+        const float a = sqrtf(s) * inv_w;
         const float d = a - sI;
         e = fmaf(d, d, e);
+        Sb[u * CB + cl] = sI / (a + eps) * f2;
+      } else {
+        const float a = sqrtf(fmaf(s, f2, eps));
+        const float d = a - sI;
+        e = fmaf(d, d, e);
+        Sb[u * CB + cl] = 2.f * (1.f - sI / a) * f2;
       }
-      z[k2] = cscale(z[k2], f);
     }
+  }
+  __syncthreads();
+  if (mode && lane < G::N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < G::N2; ++k2)
+      z[k2] = cscale(z[k2], Sb[(lane + G::N1 * k2) * CB + c]);
     inv_stepA<W>(z, lane, tw, lbuf);
   }
   __syncthreads();
@@ -600,7 +614,7 @@ Tiling make_tiling(int W, int M, bool refine) {
   const int TB = std::max(M * R * LP, M * R * W);
   t.smC = (size_t)(W + M * R * W + TB + M * R * W + (refine ? R * W : 0)) * sizeof(float2) +
           (size_t)2 * R * W * sizeof(float);
-  t.n_pmax = std::max(1, std::min(64, W * W / 1024));
+  t.n_pmax = std::max(1, std::min(1024, W * W / 256));
   return t;
 }
 
@@ -609,7 +623,9 @@ cudaError_t set_smem_limits(const Tiling& t) {
   PTY_DISPATCH_W(t.W, {
     e = cudaFuncSetAttribute(k_rows_fwd<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smA);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_cols<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smB);
+      e = cudaFuncSetAttribute(k_cols<WW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smB);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cols<WW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smB);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_rows_inv<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smC);
     if (e == cudaSuccess)
@@ -657,8 +673,18 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         float eps, float* err_part, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, npatch);
-  PTY_DISPATCH_W(t.W, (k_cols<WW><<<grid, t.thrB, t.smB, s>>>(
+  PTY_DISPATCH_W(t.W, (k_cols<WW, false><<<grid, t.thrB, t.smB, s>>>(
                           scratch, t.M, t.CB, I, ids, tw, inv_w, eps, err_part, t.npl, t.xo)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I,
+                             const int* ids, int npatch, const float2* tw, float inv_w,
+                             float delta, float* loss_part, int npl, cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  dim3 grid(t.W / t.CB, npatch);
+  PTY_DISPATCH_W(t.W, (k_cols<WW, true><<<grid, t.thrB, t.smB, s>>>(
+                          scratch, t.M, t.CB, I, ids, tw, inv_w, delta, loss_part, npl, 0)));
   return cudaGetLastError();
 }
 

@@ -93,6 +93,9 @@ _SIGS = {
                                     c_int_p]),
     "pty_fft2": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
     "pty_profile": (c_int, [c_void_p, c_int]),
+    "pty_loss": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
+    "pty_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,
+                              c_void_p, c_void_p, c_void_p]),
     "pty_get_refine_gaps": (c_int, [c_void_p, c_void_p, c_int]),
     "pty_model_intensities_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int,
                                               c_void_p, c_int, c_void_p, c_void_p]),
@@ -145,6 +148,13 @@ def _dt(name):
     import torch
     return {"u16": (np.uint16, torch.uint16), "f32": (np.float32, torch.float32),
             "c64": (np.complex64, torch.complex64), "i32": (np.int32, torch.int32)}[name]
+
+
+def _check_dev(O, P, pos):
+    import torch
+    for t, dt in ((O, torch.complex64), (P, torch.complex64), (pos, torch.float32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("expected contiguous CUDA tensors: O, P complex64, pos float32")
 
 
 def group_positions(pos, W, max_group=0, order=None):
@@ -301,6 +311,25 @@ class Problem:
         check(lib().pty_get_adam_state(self.h, m.ctypes.data, v.ctypes.data, ctypes.byref(t),
                                        ctypes.byref(it), MEM_HOST))
         return m, v, t.value, it.value
+
+    def loss(self, O, P, pos, delta=1.0):
+        """Amplitude loss of the bilinear-crop forward model (device tensors)."""
+        import torch
+        _check_dev(O, P, pos)
+        out = torch.empty(1, dtype=torch.float32, device=O.device)
+        check(lib().pty_loss(self.h, O.data_ptr(), P.data_ptr(), pos.data_ptr(), float(delta),
+                             out.data_ptr()))
+        return out
+
+    def loss_grad(self, O, P, pos, delta=1.0):
+        """(loss, dL/dO, dL/dP, dL/dpos); complex gradients as dL/dRe + i dL/dIm."""
+        import torch
+        _check_dev(O, P, pos)
+        out = torch.empty(1, dtype=torch.float32, device=O.device)
+        gO, gP, gpos = torch.empty_like(O), torch.empty_like(P), torch.empty_like(pos)
+        check(lib().pty_loss_grad(self.h, O.data_ptr(), P.data_ptr(), pos.data_ptr(), float(delta),
+                                  out.data_ptr(), gO.data_ptr(), gP.data_ptr(), gpos.data_ptr()))
+        return out, gO, gP, gpos
 
     def profile(self, mode):
         check(lib().pty_profile(self.h, int(mode)))

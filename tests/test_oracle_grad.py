@@ -65,3 +65,42 @@ def test_integer_positions_reduce_to_plain_crop():
     pos = np.floor(pos)
     o, dy, dx, (iy, ix), _ = grad.bilinear_crop(O, pos[0], 16)
     np.testing.assert_array_equal(o, O[iy:iy + 16, ix:ix + 16])
+
+
+def test_fd_on_a_32x32_crop_of_the_spiral_workload():
+    """FP64 central differences at the 256x256 / 5-mode / 10^4-position spiral
+    geometry: an object pixel of a 32x32 crop at the scan centre (the loss
+    restricted to the patches whose bilinear box covers the crop) and two
+    positions (each moves only its own patch's loss)."""
+    from paper_2205_04295_b300 import synth
+    wl = synth.spiral_256()
+    rng = np.random.Generator(np.random.PCG64(wl.seed))
+    O = synth.make_object(wl.Hy, wl.Hx, rng).astype(np.complex128)
+    P = synth.initial_probe(synth.make_probe(wl.W, wl.M, wl.photons, wl.occupancy))
+    pos = np.floor(wl.pos.astype(np.float64)) + 0.37
+    y0 = x0 = 1390
+    fl = np.floor(pos)
+    cover = np.nonzero((fl[:, 0] <= y0 + 31) & (fl[:, 0] + wl.W >= y0) &
+                       (fl[:, 1] <= x0 + 31) & (fl[:, 1] + wl.W >= x0))[0]
+    cnt, _ = synth.simulate_counts(O.astype(np.complex64), synth.make_probe(wl.W, wl.M, wl.photons, wl.occupancy),
+                                   wl.pos_true[cover], 5)
+    I = cnt.numpy().astype(np.uint16)
+    sub = pos[cover]
+    L, gO, gP, gpos = grad.loss_and_grad(O, P, sub, I, delta=1.0)
+    h = 1e-6
+    yy, xx = y0 + 13, x0 + 21
+    for comp, unit in ((np.real, 1.0), (np.imag, 1j)):
+        def f(t):
+            Oc = O.copy()
+            Oc[yy, xx] += t * unit
+            return grad.loss(Oc, P, sub, I, delta=1.0)
+        fd = central(f, 0.0, h)
+        assert np.isclose(fd, comp(gO[yy, xx]), rtol=1e-5, atol=1e-6 * abs(L))
+    for k in (0, len(sub) - 1):
+        for ax in range(2):
+            def f(t):
+                pc = sub[k:k + 1].copy()
+                pc[0, ax] += t
+                return grad.loss(O, P, pc, I[k:k + 1], delta=1.0)
+            fd = central(f, 0.0, h)
+            assert np.isclose(fd, gpos[k, ax], rtol=1e-5, atol=1e-6 * abs(L))
