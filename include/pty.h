@@ -216,6 +216,33 @@ int pty_model_intensities_noalloc(const void* O, int Hy, int Hx, const void* P,
                                   int M, int W, const float* pos, int N,
                                   float* out, void* stream);
 
+/* Batched form: many independent problems of uneven W, M and N run n_iter
+ * M-rPIE iterations each inside ONE persistent, cooperative kernel launch
+ * (captured in a CUDA graph).  A device task list interleaves the problems
+ * pass by pass; each CTA takes the next task, waits (bounded by
+ * timeout_ms on the GPU's global timer) until that problem has finished the
+ * tasks its pass depends on, and runs it.  Results equal n_iter calls of
+ * pty_run_iterations on each problem alone.  All problems use ds[0].stream.
+ * pty_batch_problem lends the i-th problem's handle (set its data, read its
+ * results; do not destroy it).  pty_batch_run returns PTY_ETIMEOUT if a wait
+ * gave up (pty_batch_status then tells which problems are incomplete). */
+typedef struct pty_batch pty_batch;
+typedef struct {
+  int split_rows;    /* tasks per row pass of a chunk (row blocks split)      */
+  int split_cols;    /* tasks per patch of a column pass (column blocks split)*/
+  int split_probe;   /* tasks per probe update                                */
+  int timeout_ms;    /* bound on every device-side dependency wait            */
+  int ctas;          /* cap on resident CTAs (0 = all that fit)               */
+  int stall_problem; /* test hook: >= 0 gives that problem a dependency that
+                        is never met, to exercise the bounded wait; -1 = off  */
+} pty_batch_schedule;
+int pty_batch_create(const pty_problem_desc* ds, int n, pty_batch** out);
+int pty_batch_problem(pty_batch* b, int i, pty_handle** h);
+int pty_batch_set_schedule(pty_batch* b, const pty_batch_schedule* s);
+int pty_batch_run(pty_batch* b, int n_iter, const pty_rpie_params* p);
+int pty_batch_status(pty_batch* b, int* per_problem);
+int pty_batch_destroy(pty_batch* b);
+
 /* Host-only greedy grouping (no GPU needed): positions pos (N*2, host),
  * boxes of side W, optional order (NULL = index order), max_group (0 =
  * unlimited).  Writes group_ptr (capacity N+1), group_pos (N), *n_groups.

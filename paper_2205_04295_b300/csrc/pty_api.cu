@@ -445,6 +445,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
                (size_t)h->Qcg * (h->M + 1)) * W2;
   const size_t nparts = (size_t)h->Qcr * h->W;  // >= Qcr * (W / RX)
   h->err_part_n = (size_t)h->N * (h->W / h->tl.CB);
+  const size_t err_part_cap = (size_t)h->N * (h->W / 2);  // any column block >= 2
   int rc = PTY_OK;
   if ((rc = alloc_into(h, h->O, (size_t)h->Hy * h->Hx)) ||
       (rc = alloc_into(h, h->P, (size_t)h->M * W2)) ||
@@ -457,7 +458,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->pden, (size_t)h->nslots * W2)) ||
       (rc = alloc_into(h, h->osum, (size_t)h->nslots)) ||
       (rc = alloc_into(h, h->omax_part, (size_t)std::max(h->Qc, h->Qcr) * nrb)) ||
-      (rc = alloc_into(h, h->err_part, h->err_part_n)) ||
+      (rc = alloc_into(h, h->err_part, err_part_cap)) ||
       (rc = alloc_into(h, h->pmax_part, (size_t)h->tl.n_pmax)) ||
       (rc = alloc_into(h, h->I, (size_t)h->N * W2)) ||
       (rc = alloc_into(h, h->pos, (size_t)2 * h->N)) ||
@@ -476,7 +477,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
   pty::make_twiddles(h->W, tw.data());
   if (cudaMemcpyAsync(h->tw, tw.data(), sizeof(float2) * h->W, cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->err_part, 0, sizeof(float) * h->err_part_n, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->err_part, 0, sizeof(float) * err_part_cap, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(PTY_ECUDA, "initial copies failed"));
@@ -949,6 +950,268 @@ int pty_group_positions(const float* pos, int N, int W, int max_group, const int
   *n_groups = (int)gptr.size() - 1;
   std::copy(gptr.begin(), gptr.end(), group_ptr);
   std::copy(gpos.begin(), gpos.end(), group_pos);
+  return PTY_OK;
+}
+
+
+// ===================================================================== batch
+struct pty_batch {
+  std::vector<pty_handle*> hs;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream to capture the graph on
+  int device = 0;
+  pty::BatchProb* probs_d = nullptr;
+  pty::BatchTask* tasks_d = nullptr;
+  size_t tasks_cap = 0;
+  unsigned* next_d = nullptr;
+  unsigned* done_d = nullptr;
+  int* error_d = nullptr;
+  std::vector<unsigned> total;
+  std::vector<int> status;
+  int ntask = 0;
+  cudaGraphExec_t gexec = nullptr;
+  pty_batch_schedule sched{4, 2, 4, 2000, 0, -1};
+  ~pty_batch() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap) cudaStreamDestroy(cap);
+    cudaFree(probs_d);
+    cudaFree(tasks_d);
+    cudaFree(next_d);
+    cudaFree(done_d);
+    cudaFree(error_d);
+    for (pty_handle* h : hs) pty_destroy(h);
+  }
+};
+
+namespace {
+void split_range(int n, int parts, std::vector<std::pair<int, int>>& out) {
+  out.clear();
+  parts = std::max(1, std::min(parts, n));
+  for (int i = 0; i < parts; ++i) {
+    const int a = (int)((long long)n * i / parts), b = (int)((long long)n * (i + 1) / parts);
+    if (b > a) out.push_back({a, b});
+  }
+}
+}  // namespace
+
+int pty_batch_create(const pty_problem_desc* ds, int n, pty_batch** out) {
+  g_err.clear();
+  if (!ds || !out || n < 1) return fail(PTY_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  pty_batch* b = new (std::nothrow) pty_batch();
+  if (!b) return fail(PTY_ENOMEM, "host allocation failed");
+  b->stream = static_cast<cudaStream_t>(ds[0].stream);
+  for (int i = 0; i < n; ++i) {
+    pty_problem_desc d = ds[i];
+    d.stream = ds[0].stream;
+    pty_handle* h = nullptr;
+    const int rc = pty_init_problem(&d, &h);
+    if (rc != PTY_OK) {
+      std::string msg = g_err;
+      delete b;
+      return fail(rc, "problem %d: %s", i, msg.c_str());
+    }
+    b->hs.push_back(h);
+  }
+  cudaGetDevice(&b->device);
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&b->probs_d, sizeof(pty::BatchProb) * n) != cudaSuccess ||
+      cudaMalloc(&b->next_d, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&b->done_d, sizeof(unsigned) * n) != cudaSuccess ||
+      cudaMalloc(&b->error_d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(PTY_ENOMEM, "batch device allocation failed");
+  }
+  b->status.assign(n, PTY_OK);
+  *out = b;
+  return PTY_OK;
+}
+
+int pty_batch_problem(pty_batch* b, int i, pty_handle** h) {
+  g_err.clear();
+  if (!b || !h || i < 0 || i >= (int)b->hs.size()) return fail(PTY_EINVAL, "bad batch index");
+  *h = b->hs[i];
+  return PTY_OK;
+}
+
+int pty_batch_set_schedule(pty_batch* b, const pty_batch_schedule* s) {
+  g_err.clear();
+  if (!b || !s) return fail(PTY_EINVAL, "null argument");
+  if (s->split_rows < 1 || s->split_cols < 1 || s->split_probe < 1 || s->timeout_ms < 1 ||
+      s->ctas < 0 || s->stall_problem >= (int)b->hs.size())
+    return fail(PTY_EINVAL, "bad schedule");
+  b->sched = *s;
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  return PTY_OK;
+}
+
+int pty_batch_run(pty_batch* b, int n_iter, const pty_rpie_params* p) {
+  g_err.clear();
+  if (!b) return fail(PTY_EINVAL, "null batch");
+  TRY(check_params(p));
+  if (n_iter < 1) return fail(PTY_EINVAL, "n_iter < 1");
+  CU(cudaSetDevice(b->device));
+  const int n = (int)b->hs.size();
+  std::vector<pty::BatchProb> probs(n);
+  std::vector<std::vector<std::vector<pty::BatchTask>>> phases(n);
+  size_t smem = 0;
+  std::vector<std::pair<int, int>> rng;
+  for (int i = 0; i < n; ++i) {
+    pty_handle* h = b->hs[i];
+    if (!h->has_data) return fail(PTY_ESTATE, "problem %d has no data", i);
+    TRY(regroup(h, p->max_group));
+    TRY(ensure_err_cap(h, n_iter));
+    const pty::Tiling t = pty::make_tiling(h->W, h->M, false, 256);
+    smem = std::max(smem, pty::batch_smem(t));
+    pty::BatchProb& pb = probs[i];
+    pb.W = h->W; pb.M = h->M; pb.N = h->N; pb.Hx = h->Hx;
+    pb.R = t.R; pb.ppc = t.ppc; pb.CB = t.CB; pb.n_pmax = t.n_pmax;
+    pb.inv_w = h->inv_w; pb.update_probe = p->update_probe; pb.a = upd_args(p);
+    pb.inv_sumI = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
+    pb.tw = h->tw; pb.O = h->O; pb.P = h->P; pb.I = h->I; pb.corners = h->corners;
+    pb.gpos = h->gpos_d; pb.scratch = h->scratch; pb.pnum = h->pnum; pb.pden = h->pden;
+    pb.osum = h->osum; pb.omax_part = h->omax_part; pb.err_part = h->err_part;
+    pb.pmax_part = h->pmax_part; pb.err_iter = h->err_iter;
+    pb.err_part_n = (size_t)h->N * (h->W / t.CB);
+    auto& ph = phases[i];
+    unsigned before = 0;
+    auto add_phase = [&](std::vector<pty::BatchTask>&& v) {
+      for (auto& tk : v) tk.need = before;
+      before += (unsigned)v.size();
+      ph.push_back(std::move(v));
+    };
+    const int G = (int)h->gptr.size() - 1;
+    for (int it = 0; it < n_iter; ++it) {
+      for (int g = 0; g < G; ++g) {
+        const int ng = h->gptr[g + 1] - h->gptr[g];
+        for (int c0 = 0; c0 < ng; c0 += h->Qc) {
+          const int nc = std::min(h->Qc, ng - c0);
+          const int off = h->gptr[g] + c0;
+          const int py = (nc + t.ppc - 1) / t.ppc;
+          for (int kind : {pty::BT_ROWS, pty::BT_COLS, pty::BT_ROWS_INV}) {
+            std::vector<pty::BatchTask> v;
+            const bool cols = kind == pty::BT_COLS;
+            const int ny = cols ? nc : py;
+            split_range(cols ? h->W / t.CB : h->W / t.R, cols ? b->sched.split_cols : b->sched.split_rows, rng);
+            for (int y = 0; y < ny; ++y)
+              for (auto& r : rng) {
+                pty::BatchTask tk{};
+                tk.prob = i; tk.kind = kind; tk.x0 = r.first; tk.x1 = r.second; tk.y = y;
+                tk.ids_off = off; tk.npatch = nc; tk.flag = (kind == pty::BT_ROWS_INV && c0 > 0);
+                v.push_back(tk);
+              }
+            add_phase(std::move(v));
+          }
+        }
+        if (p->update_probe) {
+          std::vector<pty::BatchTask> v;
+          split_range(t.n_pmax, b->sched.split_probe, rng);
+          const int used = (std::min(h->Qc, ng) + t.ppc - 1) / t.ppc;
+          for (auto& r : rng) {
+            pty::BatchTask tk{};
+            tk.prob = i; tk.kind = pty::BT_PROBE; tk.x0 = r.first; tk.x1 = r.second; tk.flag = used;
+            v.push_back(tk);
+          }
+          add_phase(std::move(v));
+        }
+      }
+      std::vector<pty::BatchTask> v(1);
+      v[0] = pty::BatchTask{};
+      v[0].prob = i; v[0].kind = pty::BT_ERR; v[0].it = it;
+      add_phase(std::move(v));
+    }
+    b->total.resize(n);
+    b->total[i] = before;
+  }
+  // interleave the problems pass by pass
+  std::vector<pty::BatchTask> tasks;
+  size_t maxph = 0;
+  for (auto& ph : phases) maxph = std::max(maxph, ph.size());
+  for (size_t f = 0; f < maxph; ++f)
+    for (int i = 0; i < n; ++i)
+      if (f < phases[i].size()) tasks.insert(tasks.end(), phases[i][f].begin(), phases[i][f].end());
+  if (b->sched.stall_problem >= 0) {
+    // test hook: a dependency that can never be met, so that the bounded
+    // wait runs out and reports PTY_ETIMEOUT instead of hanging
+    for (auto it = tasks.rbegin(); it != tasks.rend(); ++it)
+      if (it->prob == b->sched.stall_problem) {
+        it->need = 0xffffffffu;
+        break;
+      }
+  }
+  b->ntask = (int)tasks.size();
+  if (tasks.size() > b->tasks_cap) {
+    CU(cudaStreamSynchronize(b->stream));
+    cudaFree(b->tasks_d);
+    b->tasks_d = nullptr;
+    CU(cudaMalloc(&b->tasks_d, sizeof(pty::BatchTask) * tasks.size()));
+    b->tasks_cap = tasks.size();
+  }
+  CU(cudaMemcpyAsync(b->tasks_d, tasks.data(), sizeof(pty::BatchTask) * tasks.size(),
+                     cudaMemcpyHostToDevice, b->stream));
+  CU(cudaMemcpyAsync(b->probs_d, probs.data(), sizeof(pty::BatchProb) * n, cudaMemcpyHostToDevice,
+                     b->stream));
+  int ctas = 0;
+  CU(pty::batch_grid(smem, &ctas));
+  if (b->sched.ctas > 0) ctas = std::min(ctas, b->sched.ctas);
+  // one graph: reset the counters, then the persistent launch
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(b->next_d, 0, sizeof(unsigned), b->cap);
+  cudaMemsetAsync(b->done_d, 0, sizeof(unsigned) * n, b->cap);
+  cudaMemsetAsync(b->error_d, 0, sizeof(int), b->cap);
+  cudaError_t le = pty::launch_batch(b->probs_d, b->tasks_d, b->ntask, b->next_d, b->done_d,
+                                     b->error_d, (unsigned long long)b->sched.timeout_ms * 1000000ull,
+                                     ctas, smem, b->cap);
+  cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(PTY_ECUDA, "batch graph capture: %s / %s", cudaGetErrorString(le), cudaGetErrorString(ce));
+  }
+  cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(PTY_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+  for (pty_handle* h : b->hs) ++h->n_launch[PTY_K_OTHER];
+  CU(cudaGraphLaunch(b->gexec, b->stream));
+  std::vector<unsigned> done(n);
+  int err = 0;
+  CU(cudaMemcpyAsync(done.data(), b->done_d, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, b->stream));
+  CU(cudaMemcpyAsync(&err, b->error_d, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  CU(cudaStreamSynchronize(b->stream));
+  int bad = 0;
+  for (int i = 0; i < n; ++i) {
+    b->status[i] = done[i] == b->total[i] ? PTY_OK : PTY_ETIMEOUT;
+    if (b->status[i] != PTY_OK) ++bad;
+    else b->hs[i]->iter += n_iter;
+    b->hs[i]->patches += (long long)n_iter * b->hs[i]->N;
+  }
+  if (bad)
+    return fail(PTY_ETIMEOUT, "%d problem(s) did not finish: a bounded wait gave up (first on problem %d)",
+                bad, err - 1);
+  return PTY_OK;
+}
+
+int pty_batch_status(pty_batch* b, int* per_problem) {
+  g_err.clear();
+  if (!b || !per_problem) return fail(PTY_EINVAL, "null argument");
+  std::copy(b->status.begin(), b->status.end(), per_problem);
+  return PTY_OK;
+}
+
+int pty_batch_destroy(pty_batch* b) {
+  if (b) {
+    cudaSetDevice(b->device);
+    delete b;
+  }
   return PTY_OK;
 }
 

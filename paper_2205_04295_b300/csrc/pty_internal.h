@@ -29,7 +29,7 @@ bool supported_W(int W);
 
 // Record a failure message for pty_last_error() on this thread; returns code.
 int set_error(int code, const char* fmt, ...);
-Tiling make_tiling(int W, int M, bool refine = false);
+Tiling make_tiling(int W, int M, bool refine = false, int max_threads_b = 512);
 cudaError_t set_smem_limits(const Tiling& t);
 
 // Twiddle table w_W^m = exp(-2 pi i m / W), m = 0..W-1 (host, double -> float).
@@ -106,6 +106,45 @@ cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const
 cudaError_t launch_adam(float* pos, float* m, float* v, const float* g, int N, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, float max_step,
                         float ymax, float xmax, cudaStream_t s);
+
+// ---- batched persistent form (pty_batch.cu) --------------------------------
+struct BatchProb {
+  int W, M, N, Hx, R, ppc, CB, n_pmax;
+  float inv_w;
+  int update_probe;
+  UpdArgs a;
+  double inv_sumI;
+  const float2* tw;
+  float2* O;
+  float2* P;
+  const uint16_t* I;
+  const int2* corners;
+  const int* gpos;
+  float2* scratch;
+  float2* pnum;
+  float* pden;
+  float* osum;
+  float* omax_part;
+  float* err_part;
+  float* pmax_part;
+  float* err_iter;
+  size_t err_part_n;
+};
+enum { BT_ROWS = 0, BT_COLS = 1, BT_ROWS_INV = 2, BT_PROBE = 3, BT_ERR = 4 };
+struct BatchTask {
+  int prob, kind, x0, x1;   // problem, pass, tile range [x0, x1)
+  int y, ids_off, npatch, flag;  // patch sub-block, chunk offset in the group list, chunk size,
+                                 // accumulate (rows_inv) or slot count (probe)
+  unsigned need;            // tasks of this problem that must be complete first
+  int it, pad0, pad1;
+};
+size_t batch_smem(const Tiling& t);
+// Largest co-resident grid for `smem` bytes of dynamic shared memory.
+cudaError_t batch_grid(size_t smem, int* ctas);
+cudaError_t launch_batch(const BatchProb* probs, const BatchTask* tasks, int ntask,
+                         unsigned* next, unsigned* done, int* error,
+                         unsigned long long timeout_ns, int ctas, size_t smem,
+                         cudaStream_t s);
 
 cudaError_t launch_fft2(void* data, int W, int batch, int inverse,
                         const float2* tw, cudaStream_t s);

@@ -63,12 +63,11 @@ PTY_D float block_max(float v, float* red) {
 
 // ---------------------------------------------------------------- pass A
 template <int W>
-__global__ void __launch_bounds__(256)
-k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
+PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
            int M, int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
            const float2* __restrict__ tw_g, float2* __restrict__ scratch,
-           float* __restrict__ omax_part, int npl, int xo) {
+           float* __restrict__ omax_part, int npl, int xo, int bx, int by) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
@@ -76,7 +75,7 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
   float2* tbuf = Prow + M * R * W;
   __shared__ float red[32];
 
-  const int r0 = blockIdx.x * R;
+  const int r0 = bx * R;
   const int nrb = W / R;
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
@@ -90,7 +89,7 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
   const bool act = line < (M + xo) * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
-  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
   for (int lp = p0; lp < p1; ++lp) {
     const int j = ids[lp];
     const int2 cc = corners[j];
@@ -102,7 +101,7 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
-        const float2 o = __ldg(orow + c);
+        const float2 o = orow[c];
         v[n1] = k < M ? cmul(prow[c], o) : o;
         omax = fmaxf(omax, cabs2(o));
       }
@@ -117,8 +116,18 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
       for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
     }
     omax = block_max(omax, red);  // its barriers also guard lbuf reuse
-    if (threadIdx.x == 0) omax_part[(size_t)lp * nrb + blockIdx.x] = omax;
+    if (threadIdx.x == 0) omax_part[(size_t)lp * nrb + bx] = omax;
   }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256)
+k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
+           int M, int R, int ppc, const int* __restrict__ ids,
+           const int2* __restrict__ corners, int npatch,
+           const float2* __restrict__ tw_g, float2* __restrict__ scratch,
+           float* __restrict__ omax_part, int npl, int xo) {
+  rows_fwd_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, tw_g, scratch, omax_part, npl, xo, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- pass B
@@ -126,11 +135,10 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
 // domain step of the amplitude-loss adjoint, G_Psi = 2 (1 - sqrt(I) / A) Psi
 // with A = sqrt(S + eps) (eps carries delta), and the loss partial sums.
 template <int W, bool GRAD>
-__global__ void __launch_bounds__(512)
-k_cols(float2* __restrict__ scratch, int M, int CB,
+PTY_D void cols_body(float2* __restrict__ scratch, int M, int CB,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part, int npl, int xo) {
+       float* __restrict__ err_part, int npl, int xo, int bx, int by) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
@@ -139,7 +147,7 @@ k_cols(float2* __restrict__ scratch, int M, int CB,
   __shared__ float red[32];
 
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
-  const int lp = blockIdx.y, c0 = blockIdx.x * CB;
+  const int lp = by, c0 = bx * CB;
   const int c = threadIdx.x % CB, rest = threadIdx.x / CB;
   const int lane = rest % G::L, k = rest / G::L;
   // k < M: the modes; k == M (with xo): the crop, forward transform only
@@ -209,20 +217,28 @@ k_cols(float2* __restrict__ scratch, int M, int CB,
     for (int n1 = 0; n1 < G::N1; ++n1) col[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
   }
   e = block_sum(e, red);
-  if (threadIdx.x == 0) err_part[(size_t)j * (W / CB) + blockIdx.x] = e;
+  if (threadIdx.x == 0) err_part[(size_t)j * (W / CB) + bx] = e;
+}
+
+template <int W, bool GRAD>
+__global__ void __launch_bounds__(512)
+k_cols(float2* __restrict__ scratch, int M, int CB,
+       const uint16_t* __restrict__ I, const int* __restrict__ ids,
+       const float2* __restrict__ tw_g, float inv_w, float eps,
+       float* __restrict__ err_part, int npl, int xo) {
+  cols_body<W, GRAD>(scratch, M, CB, I, ids, tw_g, inv_w, eps, err_part, npl, xo, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- pass C
 template <int W>
-__global__ void __launch_bounds__(256)
-k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
+PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
            int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
-           float2* __restrict__ scratch, const float* __restrict__ omax_part,
-           const float* __restrict__ pmax_part, int n_pmax,
+           float2* scratch, const float* omax_part,
+           const float* pmax_part, int n_pmax,
            const float2* __restrict__ tw_g, UpdArgs a,
-           float2* __restrict__ pnum, float* __restrict__ pden,
-           float* __restrict__ osum, int accumulate, int npl, int refine) {
+           float2* pnum, float* pden,
+           float* osum, int accumulate, int npl, int refine, int bx, int by) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   const int TB = max(M * R * G::LP, M * R * W);
@@ -235,7 +251,7 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
   float* den = Pint + R * W;
   __shared__ float s_pmax, s_omax;
 
-  const int r0 = blockIdx.x * R;
+  const int r0 = bx * R;
   const int nrb = W / R;
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
@@ -263,7 +279,7 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
   const bool act = line < M * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
-  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
   float osum_local = 0.f;
   for (int lp = p0; lp < p1; ++lp) {
     const int j = ids[lp];
@@ -336,7 +352,7 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
       __syncthreads();
     }
   }
-  const int slot = blockIdx.y;
+  const int slot = by;
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int kk = e / (R * W), rem = e - kk * R * W, rr = rem / W, c = rem - rr * W;
     const size_t g = (((size_t)slot * M + kk) * W + r0 + rr) * W + c;
@@ -347,21 +363,33 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
     const size_t g = ((size_t)slot * W + r0 + rr) * W + c;
     pden[g] = accumulate ? pden[g] + den[e] : den[e];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0)
+  if (bx == 0 && threadIdx.x == 0)
     osum[slot] = accumulate ? osum[slot] + osum_local : osum_local;
 }
 
-// ------------------------------------------------------------- probe apply
+template <int W>
 __global__ void __launch_bounds__(256)
-k_probe_apply(float2* __restrict__ P, int M, int WW, const float2* __restrict__ pnum,
-              const float* __restrict__ pden, const float* __restrict__ osum,
-              int nslots, float alpha_P, float reg_eps, float* __restrict__ pmax_part) {
+k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
+           int R, int ppc, const int* __restrict__ ids,
+           const int2* __restrict__ corners, int npatch,
+           float2* __restrict__ scratch, const float* __restrict__ omax_part,
+           const float* __restrict__ pmax_part, int n_pmax,
+           const float2* __restrict__ tw_g, UpdArgs a,
+           float2* __restrict__ pnum, float* __restrict__ pden,
+           float* __restrict__ osum, int accumulate, int npl, int refine) {
+  rows_inv_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, scratch, omax_part, pmax_part, n_pmax, tw_g, a, pnum, pden, osum, accumulate, npl, refine, blockIdx.x, blockIdx.y);
+}
+
+// ------------------------------------------------------------- probe apply
+PTY_D void probe_apply_body(float2* P, int M, int WW, const float2* pnum, const float* pden,
+                            const float* osum, int nslots, float alpha_P, float reg_eps,
+                            float* pmax_part, int bx, int gx) {
   __shared__ float red[32];
   float os = 0.f;
   for (int s = 0; s < nslots; ++s) os += osum[s];
   const float guard = reg_eps * os;
   float lmax = 0.f;
-  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < WW; pix += gridDim.x * blockDim.x) {
+  for (int pix = bx * blockDim.x + threadIdx.x; pix < WW; pix += gx * blockDim.x) {
     float d = 0.f;
     for (int s = 0; s < nslots; ++s) d += pden[(size_t)s * WW + pix];
     const float dd = d + guard;
@@ -378,7 +406,14 @@ k_probe_apply(float2* __restrict__ P, int M, int WW, const float2* __restrict__ 
     lmax = fmaxf(lmax, pint);
   }
   lmax = block_max(lmax, red);
-  if (threadIdx.x == 0) pmax_part[blockIdx.x] = lmax;
+  if (threadIdx.x == 0) pmax_part[bx] = lmax;
+}
+
+__global__ void __launch_bounds__(256)
+k_probe_apply(float2* __restrict__ P, int M, int WW, const float2* __restrict__ pnum,
+              const float* __restrict__ pden, const float* __restrict__ osum,
+              int nslots, float alpha_P, float reg_eps, float* __restrict__ pmax_part) {
+  probe_apply_body(P, M, WW, pnum, pden, osum, nslots, alpha_P, reg_eps, pmax_part, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256)
@@ -394,8 +429,7 @@ k_pmax(const float2* __restrict__ P, int M, int WW, float* __restrict__ pmax_par
   if (threadIdx.x == 0) pmax_part[blockIdx.x] = lmax;
 }
 
-__global__ void __launch_bounds__(1024)
-k_err_reduce(const float* __restrict__ part, size_t n, double inv_sumI, float* out) {
+PTY_D void err_reduce_body(const float* part, size_t n, double inv_sumI, float* out) {
   __shared__ double red[1024];
   double s = 0.0;
   for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)part[i];
@@ -406,6 +440,11 @@ k_err_reduce(const float* __restrict__ part, size_t n, double inv_sumI, float* o
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = (float)(red[0] * inv_sumI);
+}
+
+__global__ void __launch_bounds__(1024)
+k_err_reduce(const float* __restrict__ part, size_t n, double inv_sumI, float* out) {
+  err_reduce_body(part, n, inv_sumI, out);
 }
 
 // Model intensities: forward column DFTs after pass A, S written out.
@@ -579,7 +618,7 @@ bool supported_W(int W) {
     default: return cudaErrorInvalidValue;                   \
   }
 
-Tiling make_tiling(int W, int M, bool refine) {
+Tiling make_tiling(int W, int M, bool refine, int max_threads_b) {
   Tiling t{};
   t.W = W;
   t.M = M;
@@ -601,8 +640,8 @@ Tiling make_tiling(int W, int M, bool refine) {
   while (W % R) R /= 2;
   t.R = R;
   t.ppc = 4;
-  int CB = pow2_floor(std::max(1, 512 / (MA * L)));
-  CB = std::max(2, std::min(16, CB));  // MA * CB * L <= 512 threads
+  int CB = pow2_floor(std::max(1, max_threads_b / (MA * L)));
+  CB = std::max(2, std::min(16, CB));  // MA * CB * L <= max_threads_b threads
   while ((W / 2) % CB) CB /= 2;
   t.CB = CB;
   t.thrA = round32(MA * R * L);
@@ -760,6 +799,158 @@ cudaError_t launch_finite_check(const float* p, size_t n, int* flag, cudaStream_
   if (n == 0) return cudaSuccess;
   k_finite<<<296, 256, 0, s>>>(p, n, flag);
   return cudaGetLastError();
+}
+
+
+// ===================================================================== batch
+// Many independent reconstructions in one persistent launch.  Each CTA takes
+// the next task of a global list (atomic counter), waits until its problem
+// has completed the tasks of all earlier passes (per-problem counter, acquire
+// load), runs the pass body on its tiles, and counts the task done (release).
+// The list interleaves the problems pass by pass, and every wait is for a
+// task of a smaller index, so with all CTAs resident (cooperative launch) the
+// schedule cannot deadlock; every wait is bounded anyway: past `timeout_ns`
+// of the global timer the CTA records the problem in *error and all CTAs
+// leave.
+namespace {
+
+PTY_D unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+PTY_D unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Not inlined: each pattern size keeps its own register allocation instead of
+// one allocation for all of them inside the persistent kernel.
+template <int W>
+__device__ __noinline__ void batch_task(const BatchProb& pb, const BatchTask& tk) {
+  const int* ids = pb.gpos + tk.ids_off;
+  switch (tk.kind) {
+    case BT_ROWS:
+      for (int bx = tk.x0; bx < tk.x1; ++bx) {
+        rows_fwd_body<W>(pb.O, pb.Hx, pb.P, pb.M, pb.R, pb.ppc, ids, pb.corners, tk.npatch,
+                         pb.tw, pb.scratch, pb.omax_part, pb.M, 0, bx, tk.y);
+        __syncthreads();
+      }
+      break;
+    case BT_COLS:
+      for (int bx = tk.x0; bx < tk.x1; ++bx) {
+        cols_body<W, false>(pb.scratch, pb.M, pb.CB, pb.I, ids, pb.tw, pb.inv_w, pb.a.eps,
+                            pb.err_part, pb.M, 0, bx, tk.y);
+        __syncthreads();
+      }
+      break;
+    case BT_ROWS_INV:
+      for (int bx = tk.x0; bx < tk.x1; ++bx) {
+        rows_inv_body<W>(pb.O, pb.Hx, pb.P, pb.M, pb.R, pb.ppc, ids, pb.corners, tk.npatch,
+                         pb.scratch, pb.omax_part, pb.pmax_part, pb.n_pmax, pb.tw, pb.a, pb.pnum,
+                         pb.pden, pb.osum, tk.flag, pb.M, 0, bx, tk.y);
+        __syncthreads();
+      }
+      break;
+    case BT_PROBE:
+      for (int bx = tk.x0; bx < tk.x1; ++bx) {
+        probe_apply_body(pb.P, pb.M, W * W, pb.pnum, pb.pden, pb.osum, tk.flag, pb.a.alpha_P,
+                         pb.a.reg_eps, pb.pmax_part, bx, pb.n_pmax);
+        __syncthreads();
+      }
+      break;
+    default:
+      err_reduce_body(pb.err_part, pb.err_part_n, pb.inv_sumI, pb.err_iter + tk.it);
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_batch(const BatchProb* __restrict__ probs, const BatchTask* __restrict__ tasks, int ntask,
+        unsigned* next, unsigned* done, int* error, unsigned long long timeout_ns) {
+  __shared__ int s_t, s_stop;
+  __shared__ BatchProb s_pb;  // descriptor and task live in shared memory, not registers
+  __shared__ BatchTask s_tk;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int t = (int)atomicAdd(next, 1u);
+      int stop = 1;
+      if (t < ntask) {
+        stop = 0;
+        const unsigned need = tasks[t].need;
+        const unsigned* cnt = done + tasks[t].prob;
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire_u32(cnt) < need) {
+          if (*(volatile int*)error) {
+            stop = 1;
+            break;
+          }
+          if (global_ns() - t0 > timeout_ns) {
+            atomicCAS(error, 0, 1 + tasks[t].prob);
+            stop = 1;
+            break;
+          }
+          __nanosleep(128);
+        }
+        __threadfence();
+      }
+      s_t = t;
+      s_stop = stop;
+      if (!stop) {
+        s_tk = tasks[t];
+        s_pb = probs[s_tk.prob];
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    switch (s_pb.W) {
+      case 32: batch_task<32>(s_pb, s_tk); break;
+      case 64: batch_task<64>(s_pb, s_tk); break;
+      case 96: batch_task<96>(s_pb, s_tk); break;
+      case 128: batch_task<128>(s_pb, s_tk); break;
+      case 192: batch_task<192>(s_pb, s_tk); break;
+      default: batch_task<256>(s_pb, s_tk); break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(done + s_tk.prob, 1u);
+    }
+    __syncthreads();  // s_tk / s_pb are rewritten by the next fetch
+  }
+}
+
+}  // namespace
+
+size_t batch_smem(const Tiling& t) { return std::max(std::max(t.smA, t.smB), t.smC); }
+
+cudaError_t batch_grid(size_t smem, int* ctas) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, 256, smem)) != cudaSuccess)
+    return e;
+  *ctas = std::max(1, per) * sms;
+  return cudaSuccess;
+}
+
+cudaError_t launch_batch(const BatchProb* probs, const BatchTask* tasks, int ntask,
+                         unsigned* next, unsigned* done, int* error,
+                         unsigned long long timeout_ns, int ctas, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batch, probs, tasks, ntask, next, done, error, timeout_ns);
 }
 
 }  // namespace pty

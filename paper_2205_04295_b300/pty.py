@@ -59,6 +59,11 @@ class Stats(ctypes.Structure):
                 "patches": int(self.patches)}
 
 
+class BatchSchedule(ctypes.Structure):
+    _fields_ = [("split_rows", c_int), ("split_cols", c_int), ("split_probe", c_int),
+                ("timeout_ms", c_int), ("ctas", c_int), ("stall_problem", c_int)]
+
+
 def rpie_params(alpha_O=1.0, alpha_P=1.0, beta=1.0, gamma=0.1, eps=1.0, reg_eps=1e-12,
                 max_group=0, update_probe=True):
     return RpieParams(alpha_O, alpha_P, beta, gamma, eps, reg_eps, max_group, int(update_probe))
@@ -93,6 +98,12 @@ _SIGS = {
                                     c_int_p]),
     "pty_fft2": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
     "pty_profile": (c_int, [c_void_p, c_int]),
+    "pty_batch_create": (c_int, [ctypes.POINTER(ProblemDesc), c_int, ctypes.POINTER(c_void_p)]),
+    "pty_batch_problem": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p)]),
+    "pty_batch_set_schedule": (c_int, [c_void_p, ctypes.POINTER(BatchSchedule)]),
+    "pty_batch_run": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams)]),
+    "pty_batch_status": (c_int, [c_void_p, c_void_p]),
+    "pty_batch_destroy": (c_int, [c_void_p]),
     "pty_loss": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
     "pty_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_void_p,
                               c_void_p, c_void_p, c_void_p]),
@@ -343,3 +354,65 @@ class Problem:
         m = np.ascontiguousarray(m, np.float32)
         v = np.ascontiguousarray(v, np.float32)
         check(lib().pty_set_adam_state(self.h, m.ctypes.data, v.ctypes.data, t, it, MEM_HOST))
+
+
+class _Borrowed(Problem):
+    """A Problem view of a handle owned by a Batch (never destroyed here)."""
+
+    def __init__(self, h, W, M, N, Hy, Hx, stream):
+        self.W, self.M, self.N, self.Hy, self.Hx = W, M, N, Hy, Hx
+        self.stream = stream
+        self.h = h
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Many independent problems run by one persistent graph-captured launch."""
+
+    def __init__(self, shapes, stream=None, scratch_bytes=0):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        n = len(shapes)
+        arr = (ProblemDesc * n)()
+        for i, (W, M, N, Hy, Hx) in enumerate(shapes):
+            arr[i] = ProblemDesc(W, M, N, Hy, Hx, c_void_p(stream.cuda_stream), ALLOC_FN(),
+                                 FREE_FN(), None, scratch_bytes, 0)
+        b = c_void_p()
+        check(lib().pty_batch_create(arr, n, ctypes.byref(b)))
+        self.b = b
+        self.problems = []
+        for i, shp in enumerate(shapes):
+            h = c_void_p()
+            check(lib().pty_batch_problem(b, i, ctypes.byref(h)))
+            self.problems.append(_Borrowed(h, *shp, stream))
+
+    def schedule(self, split_rows=4, split_cols=2, split_probe=4, timeout_ms=2000, ctas=0,
+                 stall_problem=-1):
+        sc = BatchSchedule(split_rows, split_cols, split_probe, timeout_ms, ctas, stall_problem)
+        check(lib().pty_batch_set_schedule(self.b, ctypes.byref(sc)))
+
+    def run(self, n_iter, params=None):
+        params = params or rpie_params()
+        check(lib().pty_batch_run(self.b, n_iter, ctypes.byref(params)))
+
+    def status(self):
+        st = np.zeros(len(self.problems), np.int32)
+        check(lib().pty_batch_status(self.b, st.ctypes.data))
+        return st
+
+    def close(self):
+        if getattr(self, "b", None):
+            for p in self.problems:
+                p.close()
+            lib().pty_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
