@@ -237,6 +237,8 @@ def run_ours(args, wl, rank, world, local):
 
     prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx, stream=stream)
     prob.set_data(I_dev, pos_dev, O0_dev, P0_dev)
+    from paper_2205_04295_b300 import autotune
+    tiling = autotune.apply(prob)
     n_groups = len(prob.groups())
 
     # ---- device-resident timing (inputs already in HBM)
@@ -314,11 +316,13 @@ def run_ours(args, wl, rank, world, local):
     h2d = I_h.numel() * 2 + pos_h.numel() * 4 + O0_h.numel() * 8 + P0_h.numel() * 8
     d2h = O_out.numel() * 8 + P_out.numel() * 8
 
+    batch = run_batch_measure(args, dev) if not args.no_batch else None
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": wl.name, "W": wl.W, "M": wl.M, "N": wl.N,
-                      "object": [wl.Hy, wl.Hx], "groups": n_groups,
+                      "object": [wl.Hy, wl.Hx], "groups": n_groups, "tiling": tiling,
                       "schedule": "greedy disjoint groups, index order",
                       "l2": "no flush: every step streams the %.2f GB pattern stack (> 126 MB L2)"
                             % (wl.N * wl.W * wl.W * 2 / 1e9),
@@ -334,11 +338,39 @@ def run_ours(args, wl, rank, world, local):
            "gpu_launches": launches,
            "grad": {"ms_per_step": grad_ms, "unit": "ms",
                     "what": "loss and dL/dO, dL/dP, dL/dpos over all positions, bilinear crops"},
+           "batch": batch,
            "e2e": {"value": world * wl.N * e2e_steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "clocks": clk.summary()}
     prob.close()
     return out
+
+
+def run_batch_measure(args, dev, n_iter=5):
+    """The 64-problem uneven batch (W in {64,96,128,192}, N 50..900, M 1..3)
+    in one persistent graph-captured launch: aggregate pattern-updates/s."""
+    import torch
+    from paper_2205_04295_b300 import pty, synth
+    wls = [synth.batch_problem(p) for p in range(64)]
+    b = pty.Batch([(w.W, w.M, w.N, w.Hy, w.Hx) for w in wls])
+    for w, p in zip(wls, b.problems):
+        d = synth.build(w, device=dev)
+        p.set_data(synth.counts_u16(d["I"]), torch.from_numpy(d["pos"]).to(dev),
+                   torch.from_numpy(d["O0"]).to(dev), torch.from_numpy(d["P0"]).to(dev))
+    prm = pty.rpie_params()
+    b.run(1, prm)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    b.run(n_iter, prm)
+    e.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e)
+    n = sum(w.N for w in wls) * n_iter
+    b.close()
+    return {"problems": 64, "iterations": n_iter, "pattern_updates": n, "ms": ms,
+            "value": n / (ms / 1e3), "unit": UNIT, "launches": 1,
+            "what": "one persistent cooperative launch (a CUDA graph) for all problems and iterations"}
 
 
 def main():
@@ -349,6 +381,7 @@ def main():
     ap.add_argument("--workload", default="spiral_256")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     wl = workloads()[args.workload]()

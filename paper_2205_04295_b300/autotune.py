@@ -1,0 +1,164 @@
+"""Project autotuner for the launch geometry of the M-rPIE passes.
+
+For a (W, M) class it searches, in stages, the tiling of one problem:
+  1. CB, columns per CTA of the column pass;
+  2. R x ppc, rows and patches per CTA of the two row passes;
+  3. the far-field scratch budget (the chunk of a group held in L2);
+timing one full iteration per candidate with CUDA events on the library's
+stream (results never depend on the tiling beyond the summation order of the
+probe sums).  For the batched form it searches the task granularity (how many
+tasks a pass of one chunk is split into).  Winners are cached in JSON
+(``tuning.json`` beside this file) keyed "W x M".
+
+    python -m paper_2205_04295_b300.autotune [--classes 256x5,64x1,...] [--out FILE]
+"""
+import argparse
+import json
+import os
+
+from . import pty
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+LANES = {32: 8, 64: 8, 96: 12, 128: 16, 192: 16, 256: 16}
+
+
+def _pow2(lo, hi):
+    v = lo
+    while v <= hi:
+        yield v
+        v *= 2
+
+
+def candidates(W, M):
+    L = LANES[W]
+    Rs = [r for r in _pow2(1, 16) if W % r == 0 and M * r * L <= 256]
+    CBs = [c for c in _pow2(2, 16) if (W // 2) % c == 0 and M * c * L <= 512]
+    return Rs, [1, 2, 4, 8], CBs, [32 << 20, 64 << 20, 96 << 20]
+
+
+def time_iteration(prob, params, reps=2):
+    """Milliseconds of one iteration (median of reps, after one warm-up)."""
+    import torch
+    prob.run(1, params, errors=False)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(prob.stream)
+        prob.run(1, params, errors=False)
+        b.record(prob.stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def tune_problem(prob, params=None, reps=2):
+    """Staged search on one problem (its data already set).  Returns a dict
+    with the best tiling, its time and every trial."""
+    params = params or pty.rpie_params()
+    Rs, ppcs, CBs, budgets = candidates(prob.W, prob.M)
+    best = dict(prob.tiling())
+    best["scratch_bytes"] = 64 << 20
+    trials = []
+
+    def trial(**t):
+        cfg = dict(best)
+        cfg.update(t)
+        prob.set_tiling(cfg["R"], cfg["ppc"], cfg["CB"], cfg["scratch_bytes"])
+        ms = time_iteration(prob, params, reps)
+        trials.append(dict(cfg, ms=ms))
+        return ms, cfg
+
+    for stage in (
+        [dict(CB=c) for c in CBs],
+        [dict(R=r, ppc=q) for r in Rs for q in ppcs],
+        [dict(scratch_bytes=b) for b in budgets],
+    ):
+        results = [trial(**t) for t in stage]
+        ms, cfg = min(results, key=lambda x: x[0])
+        best = cfg
+        best_ms = ms
+    prob.set_tiling(best["R"], best["ppc"], best["CB"], best["scratch_bytes"])
+    return {"tiling": best, "ms": best_ms, "trials": trials}
+
+
+def tune_batch(batch, n_iter=1, params=None):
+    """Task granularity of the batched form: returns the best schedule."""
+    import time
+    import torch
+    params = params or pty.rpie_params()
+    best = None
+    for sr, sc, sp in ((1, 1, 1), (2, 1, 2), (4, 2, 4), (8, 2, 4), (8, 4, 8), (16, 8, 8)):
+        batch.schedule(split_rows=sr, split_cols=sc, split_probe=sp)
+        batch.run(n_iter, params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch.run(n_iter, params)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if best is None or dt < best[0]:
+            best = (dt, dict(split_rows=sr, split_cols=sc, split_probe=sp))
+    batch.schedule(**best[1])
+    return {"schedule": best[1], "s": best[0]}
+
+
+def load(path=CACHE):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def save(table, path=CACHE):
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+
+
+def apply(prob, table=None):
+    """Apply the cached tiling of prob's (W, M) class, if any; returns it."""
+    table = load() if table is None else table
+    ent = table.get("%dx%d" % (prob.W, prob.M))
+    if ent:
+        t = ent["tiling"]
+        prob.set_tiling(t["R"], t["ppc"], t["CB"], t["scratch_bytes"])
+        return t
+    return None
+
+
+def _workload(W, M):
+    from . import synth
+    if W == 256:
+        return synth.spiral_256(n=3000)
+    n = 14 if W <= 96 else 10
+    return synth.tiny(W=W, M=M, ny=n, nx=n, step=W / 8.0, seed=900 + W + M, photons=1e6,
+                      jitter=2.0)
+
+
+def main():
+    import torch
+    from . import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--classes", default="256x5,64x1,64x2,64x3,96x1,96x2,96x3,128x1,128x2,"
+                                        "128x3,192x1,192x2,192x3")
+    ap.add_argument("--out", default=CACHE)
+    args = ap.parse_args()
+    table = load(args.out)
+    for cls in args.classes.split(","):
+        W, M = (int(v) for v in cls.split("x"))
+        wl = _workload(W, M)
+        d = synth.build(wl, device="cuda")
+        prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
+        prob.set_data(synth.counts_u16(d["I"]), torch.from_numpy(d["pos"]).cuda(),
+                      torch.from_numpy(d["O0"]).cuda(), torch.from_numpy(d["P0"]).cuda())
+        res = tune_problem(prob)
+        res["workload"] = wl.name
+        table[cls] = res
+        print(cls, res["tiling"], "%.3f ms" % res["ms"], flush=True)
+        prob.close()
+    save(table, args.out)
+
+
+if __name__ == "__main__":
+    main()

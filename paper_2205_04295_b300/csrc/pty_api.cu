@@ -904,6 +904,65 @@ int pty_model_intensities(pty_handle* h, float* dst, int mem_kind) {
   return rc;
 }
 
+int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  if (!t) return fail(PTY_EINVAL, "null tiling");
+  const int W = h->W, M = h->M, L = pty::lanes_per_line(W);
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  if (t->R && (!pow2(t->R) || W % t->R || M * t->R * L > 256))
+    return fail(PTY_EINVAL, "rows per CTA R=%d invalid for W=%d, M=%d", t->R, W, M);
+  if (t->CB && (!pow2(t->CB) || t->CB < 2 || (W / 2) % t->CB || M * t->CB * L > 512))
+    return fail(PTY_EINVAL, "columns per CTA CB=%d invalid for W=%d, M=%d", t->CB, W, M);
+  if (t->ppc < 0 || t->ppc > 64) return fail(PTY_EINVAL, "patches per CTA %d", t->ppc);
+  pty::Tiling nt = pty::make_tiling(W, M, false, 512, t->R, t->ppc, t->CB);
+  if (nt.smA > 227 * 1024 || nt.smB > 227 * 1024 || nt.smC > 227 * 1024)
+    return fail(PTY_EINVAL, "tiling needs too much shared memory");
+  const size_t W2 = (size_t)W * W;
+  const size_t budget = t->scratch_bytes ? t->scratch_bytes : ((size_t)64 << 20);
+  const int Qc = (int)std::min<size_t>((size_t)h->N, std::max<size_t>(1, budget / (W2 * M * sizeof(float2))));
+  // grow the buffers whose size depends on the tiling
+  const int nslots = (std::max(std::max(Qc, h->Qcr), h->Qcg) + nt.ppc - 1) / nt.ppc;
+  const size_t scratch = std::max(std::max((size_t)Qc * M, (size_t)h->Qcr * h->tlr.npl),
+                                  (size_t)h->Qcg * (M + 1)) * W2;
+  const size_t cur_scratch = std::max(std::max((size_t)h->Qc * M, (size_t)h->Qcr * h->tlr.npl),
+                                      (size_t)h->Qcg * (M + 1)) * W2;
+  CU(cudaStreamSynchronize(h->stream));
+  if (scratch > cur_scratch) {
+    h->dfree(h->scratch);
+    h->scratch = nullptr;
+    TRY(alloc_into(h, h->scratch, scratch));
+  }
+  if (nslots > h->nslots) {
+    h->dfree(h->pnum); h->dfree(h->pden); h->dfree(h->osum);
+    h->pnum = nullptr; h->pden = nullptr; h->osum = nullptr;
+    TRY(alloc_into(h, h->pnum, (size_t)nslots * M * W2));
+    TRY(alloc_into(h, h->pden, (size_t)nslots * W2));
+    TRY(alloc_into(h, h->osum, (size_t)nslots));
+    h->nslots = nslots;
+  }
+  const size_t omax_need = (size_t)std::max(Qc, h->Qcr) * (W / std::min(nt.R, h->tlr.R));
+  h->dfree(h->omax_part);
+  h->omax_part = nullptr;
+  TRY(alloc_into(h, h->omax_part, std::max(omax_need, (size_t)std::max(h->Qc, h->Qcr) * W)));
+  h->tl = nt;
+  h->Qc = Qc;
+  h->err_part_n = (size_t)h->N * (W / nt.CB);
+  CU(pty::set_smem_limits(h->tl));
+  CU(pty::set_grad_smem(h->tl));
+  return PTY_OK;
+}
+
+int pty_get_tiling(pty_handle* h, pty_tiling* t) {
+  g_err.clear();
+  if (!h || !t) return fail(PTY_EINVAL, "null argument");
+  t->R = h->tl.R;
+  t->ppc = h->tl.ppc;
+  t->CB = h->tl.CB;
+  t->scratch_bytes = (size_t)h->Qc * h->M * h->W * h->W * sizeof(float2);
+  return PTY_OK;
+}
+
 int pty_profile(pty_handle* h, int mode) {
   g_err.clear();
   if (!h) return fail(PTY_EINVAL, "null handle");

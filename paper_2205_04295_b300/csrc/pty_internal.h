@@ -29,7 +29,10 @@ bool supported_W(int W);
 
 // Record a failure message for pty_last_error() on this thread; returns code.
 int set_error(int code, const char* fmt, ...);
-Tiling make_tiling(int W, int M, bool refine = false, int max_threads_b = 512);
+// R_req / ppc_req / CB_req > 0 override the defaults (callers validate them).
+Tiling make_tiling(int W, int M, bool refine = false, int max_threads_b = 512, int R_req = 0,
+                   int ppc_req = 0, int CB_req = 0);
+int lanes_per_line(int W);
 cudaError_t set_smem_limits(const Tiling& t);
 
 // Twiddle table w_W^m = exp(-2 pi i m / W), m = 0..W-1 (host, double -> float).

@@ -603,6 +603,19 @@ template <int W> void geo(int& L, int& LP) {
 
 }  // namespace
 
+int lanes_per_line(int W) {
+  int L = 16, LP = 0;
+  switch (W) {
+    case 32: geo<32>(L, LP); break;
+    case 64: geo<64>(L, LP); break;
+    case 96: geo<96>(L, LP); break;
+    case 128: geo<128>(L, LP); break;
+    case 192: geo<192>(L, LP); break;
+    default: geo<256>(L, LP); break;
+  }
+  return L;
+}
+
 bool supported_W(int W) {
   return W == 32 || W == 64 || W == 96 || W == 128 || W == 192 || W == 256;
 }
@@ -618,7 +631,8 @@ bool supported_W(int W) {
     default: return cudaErrorInvalidValue;                   \
   }
 
-Tiling make_tiling(int W, int M, bool refine, int max_threads_b) {
+Tiling make_tiling(int W, int M, bool refine, int max_threads_b, int R_req, int ppc_req,
+                   int CB_req) {
   Tiling t{};
   t.W = W;
   t.M = M;
@@ -638,11 +652,13 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b) {
   int R = pow2_floor(std::max(1, 256 / (MA * L)));
   R = std::min(R, 16);
   while (W % R) R /= 2;
+  if (R_req > 0) R = R_req;
   t.R = R;
-  t.ppc = 4;
+  t.ppc = ppc_req > 0 ? ppc_req : 4;
   int CB = pow2_floor(std::max(1, max_threads_b / (MA * L)));
   CB = std::max(2, std::min(16, CB));  // MA * CB * L <= max_threads_b threads
   while ((W / 2) % CB) CB /= 2;
+  if (CB_req > 0) CB = CB_req;
   t.CB = CB;
   t.thrA = round32(MA * R * L);
   t.thrC = round32(M * R * L);

@@ -59,6 +59,10 @@ class Stats(ctypes.Structure):
                 "patches": int(self.patches)}
 
 
+class Tiling(ctypes.Structure):
+    _fields_ = [("R", c_int), ("ppc", c_int), ("CB", c_int), ("scratch_bytes", c_size_t)]
+
+
 class BatchSchedule(ctypes.Structure):
     _fields_ = [("split_rows", c_int), ("split_cols", c_int), ("split_probe", c_int),
                 ("timeout_ms", c_int), ("ctas", c_int), ("stall_problem", c_int)]
@@ -98,6 +102,8 @@ _SIGS = {
                                     c_int_p]),
     "pty_fft2": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
     "pty_profile": (c_int, [c_void_p, c_int]),
+    "pty_set_tiling": (c_int, [c_void_p, ctypes.POINTER(Tiling)]),
+    "pty_get_tiling": (c_int, [c_void_p, ctypes.POINTER(Tiling)]),
     "pty_batch_create": (c_int, [ctypes.POINTER(ProblemDesc), c_int, ctypes.POINTER(c_void_p)]),
     "pty_batch_problem": (c_int, [c_void_p, c_int, ctypes.POINTER(c_void_p)]),
     "pty_batch_set_schedule": (c_int, [c_void_p, ctypes.POINTER(BatchSchedule)]),
@@ -341,6 +347,14 @@ class Problem:
         check(lib().pty_loss_grad(self.h, O.data_ptr(), P.data_ptr(), pos.data_ptr(), float(delta),
                                   out.data_ptr(), gO.data_ptr(), gP.data_ptr(), gpos.data_ptr()))
         return out, gO, gP, gpos
+
+    def set_tiling(self, R=0, ppc=0, CB=0, scratch_bytes=0):
+        check(lib().pty_set_tiling(self.h, ctypes.byref(Tiling(R, ppc, CB, scratch_bytes))))
+
+    def tiling(self):
+        t = Tiling()
+        check(lib().pty_get_tiling(self.h, ctypes.byref(t)))
+        return {"R": t.R, "ppc": t.ppc, "CB": t.CB, "scratch_bytes": int(t.scratch_bytes)}
 
     def profile(self, mode):
         check(lib().pty_profile(self.h, int(mode)))

@@ -211,3 +211,22 @@ def test_full_size_spiral_sampled_groups():
     assert rel_l2(Og, st.O) <= TOL1
     assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= 2e-4
     assert rel_l2(prob.probe(False), st.P) <= TOL1
+
+
+def test_tiling_overrides_keep_parity_and_bad_ones_are_rejected():
+    from paper_2205_04295_b300 import pty
+    wl = synth.tiny(W=128, M=3, ny=4, nx=4, step=16.0, seed=19, photons=1e6)
+    d = build(wl)
+    ref = gpu_problem(wl, d)
+    ref.run(2)
+    for R, ppc, CB, sb in ((1, 1, 2, 0), (4, 8, 8, 3 * 3 * 128 * 128 * 8), (2, 2, 4, 96 << 20)):
+        prob = gpu_problem(wl, d)
+        prob.set_tiling(R, ppc, CB, sb)
+        assert prob.tiling()["R"] == R and prob.tiling()["CB"] == CB
+        prob.run(2)
+        assert rel_l2(prob.object(False), ref.object(False)) <= 1e-6
+        assert rel_l2(prob.probe(False), ref.probe(False)) <= 1e-6
+    for bad in ((3, 0, 0), (32, 0, 0), (0, 0, 3), (0, 0, 128), (0, -1, 0)):
+        with pytest.raises(pty.PtyError) as e:
+            ref.set_tiling(*bad)
+        assert e.value.code == pty.PTY_EINVAL
