@@ -264,6 +264,18 @@ def run_ours(args, wl, rank, world, local):
     value = world * wl.N * args.steps / (ms / 1e3)
     launches = sum(st["launches"].values())
 
+    # ---- the same step with XCORR_A registration and the Adam position step on
+    rp = pty.refine_params(upsample=20, lr=0.5, start_iter=0)
+    prob.refine(1, prm, rp, errors=False)
+    torch.cuda.synchronize()
+    rsteps = max(1, min(args.steps, 3))
+    start.record(stream)
+    prob.refine(rsteps, prm, rp, errors=False)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    refine_ms = max_over_ranks(start.elapsed_time(stop) / rsteps, world)
+    prob.set_positions(pos_dev)
+
     # ---- per-kernel durations, CUDA events on the library's stream
     prob.profile(1)
     prob.run(1, prm, errors=False)
@@ -339,6 +351,8 @@ def run_ours(args, wl, rank, world, local):
            "grad": {"ms_per_step": grad_ms, "unit": "ms",
                     "what": "loss and dL/dO, dL/dP, dL/dpos over all positions, bilinear crops"},
            "batch": batch,
+           "refine": {"value": world * wl.N / (refine_ms / 1e3), "unit": UNIT, "ms_per_step": refine_ms,
+                      "what": "same step with XCORR_A registration (U = 20) and one Adam step per position"},
            "e2e": {"value": world * wl.N * e2e_steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "clocks": clk.summary()}

@@ -468,7 +468,9 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->corners, (size_t)h->N)) ||
       (rc = alloc_into(h, h->gpos_d, (size_t)h->N)) ||
       (rc = alloc_into(h, h->ggpos_d, (size_t)h->N)) ||
-      (rc = alloc_into(h, h->gpos_part, (size_t)h->N * (h->W / h->tl.R) * 2)) ||
+      // dL/dpos partials: one pair per position and row block; sized for any
+      // row-block height R >= 1 so that pty_set_tiling never outgrows it
+      (rc = alloc_into(h, h->gpos_part, (size_t)h->N * h->W * 2)) ||
       (rc = alloc_into(h, h->iota, (size_t)h->N)) ||
       (rc = alloc_into(h, h->flag, (size_t)4)) ||
       (rc = alloc_into(h, h->sum_d, (size_t)1)))
@@ -922,7 +924,9 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   const size_t budget = t->scratch_bytes ? t->scratch_bytes : ((size_t)64 << 20);
   const int Qc = (int)std::min<size_t>((size_t)h->N, std::max<size_t>(1, budget / (W2 * M * sizeof(float2))));
   // grow the buffers whose size depends on the tiling
-  const int nslots = (std::max(std::max(Qc, h->Qcr), h->Qcg) + nt.ppc - 1) / nt.ppc;
+  // slots for this ppc and for the default ppc (4) the batched form uses
+  const int ppc_min = std::min(nt.ppc, 4);
+  const int nslots = (std::max(std::max(Qc, h->Qcr), h->Qcg) + ppc_min - 1) / ppc_min;
   const size_t scratch = std::max(std::max((size_t)Qc * M, (size_t)h->Qcr * h->tlr.npl),
                                   (size_t)h->Qcg * (M + 1)) * W2;
   const size_t cur_scratch = std::max(std::max((size_t)h->Qc * M, (size_t)h->Qcr * h->tlr.npl),

@@ -124,3 +124,19 @@ def test_full_size_spiral_sampled_gradient():
     assert len(cover) > 20
     _, gOo, _, _ = grad.loss_and_grad(d["O_true"], d["P0"], posd[cover], Ih[cover], delta=1.0)
     assert rel_l2(gO[y0:y0 + 32, x0:x0 + 32], gOo[y0:y0 + 32, x0:x0 + 32]) <= 1e-5
+
+
+def test_gradient_under_non_default_tilings():
+    """Every buffer indexed by row block must fit the smallest row block."""
+    wl = synth.tiny(W=64, M=3, ny=4, nx=4, step=20.0, seed=45, photons=1e6)
+    wl.Hy += 2
+    wl.Hx += 2
+    d = build(wl)
+    O, P, pos = state(wl, d)
+    prob, t, ref = gpu_grad(wl, d, O, P, pos)
+    for R, ppc, CB in ((1, 8, 4), (1, 1, 2), (2, 4, 16)):
+        prob.set_tiling(R, ppc, CB, 0)
+        got = [to_host(x) for x in prob.loss_grad(*t)]
+        assert abs(got[0][0] - ref[0][0]) <= 1e-5 * abs(ref[0][0])
+        for a, b in zip(got[1:], ref[1:]):
+            assert rel_l2(a, b) <= 1e-5
