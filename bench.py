@@ -276,6 +276,18 @@ def run_ours(args, wl, rank, world, local):
     refine_ms = max_over_ranks(start.elapsed_time(stop) / rsteps, world)
     prob.set_positions(pos_dev)
 
+    # ---- the unfused torch + cuFFT form of the same schedule (comparison)
+    from paper_2205_04295_b300.unfused import UnfusedRPIE
+    unf = UnfusedRPIE(O0_dev, P0_dev, I_dev.to(torch.int32), pos_dev, wl.W)
+    unf.iteration()
+    torch.cuda.synchronize()
+    start.record(stream)
+    unf.iteration()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    unfused_ms = max_over_ranks(start.elapsed_time(stop), world)
+    del unf
+
     # ---- per-kernel durations, CUDA events on the library's stream
     prob.profile(1)
     prob.run(1, prm, errors=False)
@@ -351,6 +363,9 @@ def run_ours(args, wl, rank, world, local):
            "grad": {"ms_per_step": grad_ms, "unit": "ms",
                     "what": "loss and dL/dO, dL/dP, dL/dpos over all positions, bilinear crops"},
            "batch": batch,
+           "unfused_cufft": {"value": world * wl.N / (unfused_ms / 1e3), "unit": UNIT,
+                             "ms_per_step": unfused_ms,
+                             "what": "same schedule as stock torch ops + cuFFT (comparison form)"},
            "refine": {"value": world * wl.N / (refine_ms / 1e3), "unit": UNIT, "ms_per_step": refine_ms,
                       "what": "same step with XCORR_A registration (U = 20) and one Adam step per position"},
            "e2e": {"value": world * wl.N * e2e_steps / e2e_s, "unit": UNIT,

@@ -163,14 +163,16 @@ int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t,
                        int iter, int mem_kind);
 
 /* Launch geometry of the plain M-rPIE passes, for tuning (0 = default):
- * R rows per CTA of the row passes ((M) * R * lanes <= 256 threads), ppc
- * patches per CTA of the row passes, CB columns per CTA of the column pass,
- * scratch_bytes the far-field chunk budget.  Results do not depend on the
+ * R rows per CTA of the row passes (M * R * lanes <= 256 threads), ppc
+ * patches per CTA of the row passes, CB columns per CTA of the column pass
+ * (M * CB * lanes <= 384 threads), scratch_bytes the far-field chunk budget,
+ * ppcb patches per CTA of the column pass.  Results do not depend on the
  * tiling except through the summation order of the probe sums.  The
  * project's autotuner (paper_2205_04295_b300/autotune.py) searches these. */
 typedef struct {
   int R, ppc, CB;
   size_t scratch_bytes;
+  int ppcb;         /* patches per CTA of the column pass (0 = default) */
 } pty_tiling;
 int pty_set_tiling(pty_handle* h, const pty_tiling* t);
 int pty_get_tiling(pty_handle* h, pty_tiling* t);

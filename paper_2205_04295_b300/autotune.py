@@ -32,8 +32,8 @@ def _pow2(lo, hi):
 def candidates(W, M):
     L = LANES[W]
     Rs = [r for r in _pow2(1, 16) if W % r == 0 and M * r * L <= 256]
-    CBs = [c for c in _pow2(2, 16) if (W // 2) % c == 0 and M * c * L <= 512]
-    return Rs, [1, 2, 4, 8], CBs, [32 << 20, 64 << 20, 96 << 20]
+    CBs = [c for c in _pow2(2, 16) if (W // 2) % c == 0 and M * c * L <= 384]
+    return Rs, [1, 2, 4, 8, 16], CBs, [32 << 20, 64 << 20, 96 << 20], [1, 2, 4]
 
 
 def time_iteration(prob, params, reps=2):
@@ -57,7 +57,7 @@ def tune_problem(prob, params=None, reps=2):
     """Staged search on one problem (its data already set).  Returns a dict
     with the best tiling, its time and every trial."""
     params = params or pty.rpie_params()
-    Rs, ppcs, CBs, budgets = candidates(prob.W, prob.M)
+    Rs, ppcs, CBs, budgets, ppcbs = candidates(prob.W, prob.M)
     best = dict(prob.tiling())
     best["scratch_bytes"] = 64 << 20
     trials = []
@@ -65,13 +65,13 @@ def tune_problem(prob, params=None, reps=2):
     def trial(**t):
         cfg = dict(best)
         cfg.update(t)
-        prob.set_tiling(cfg["R"], cfg["ppc"], cfg["CB"], cfg["scratch_bytes"])
+        prob.set_tiling(cfg["R"], cfg["ppc"], cfg["CB"], cfg["scratch_bytes"], cfg["ppcb"])
         ms = time_iteration(prob, params, reps)
         trials.append(dict(cfg, ms=ms))
         return ms, cfg
 
     for stage in (
-        [dict(CB=c) for c in CBs],
+        [dict(CB=c, ppcb=q) for c in CBs for q in ppcbs],
         [dict(R=r, ppc=q) for r in Rs for q in ppcs],
         [dict(scratch_bytes=b) for b in budgets],
     ):
@@ -79,7 +79,7 @@ def tune_problem(prob, params=None, reps=2):
         ms, cfg = min(results, key=lambda x: x[0])
         best = cfg
         best_ms = ms
-    prob.set_tiling(best["R"], best["ppc"], best["CB"], best["scratch_bytes"])
+    prob.set_tiling(best["R"], best["ppc"], best["CB"], best["scratch_bytes"], best["ppcb"])
     return {"tiling": best, "ms": best_ms, "trials": trials}
 
 
@@ -122,7 +122,7 @@ def apply(prob, table=None):
     ent = table.get("%dx%d" % (prob.W, prob.M))
     if ent:
         t = ent["tiling"]
-        prob.set_tiling(t["R"], t["ppc"], t["CB"], t["scratch_bytes"])
+        prob.set_tiling(t["R"], t["ppc"], t["CB"], t["scratch_bytes"], t.get("ppcb", 0))
         return t
     return None
 

@@ -145,6 +145,7 @@ struct pty_handle {
   int Qc = 1, Qcr = 1, nslots = 1;
   pty::RefGeo rg{};
   float2* roots = nullptr;
+  float2* upart = nullptr;  // fine-grid partial sums of the registration
   int roots_U = 0;
   float *cval = nullptr, *gap = nullptr;
   int* cidx = nullptr;
@@ -349,7 +350,7 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, bool refine = fals
       CU(pty::launch_xcorr_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->cval, h->cidx,
                                 h->stream));
       CU(pty::launch_updft(h->rg, h->scratch, tl.npl, h->M, idc, nc, h->cval, h->cidx,
-                           h->roots, h->shift, h->gap, h->stream));
+                           h->roots, h->upart, h->shift, h->gap, h->stream));
       h->n_launch[PTY_K_REFINE] += 2;
     }
   }
@@ -599,6 +600,9 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
     std::vector<float2> roots((size_t)h->rg.U * h->W);
     pty::make_up_roots(h->W, h->rg.U, roots.data());
     TRY(alloc_into(h, h->roots, roots.size()));
+    if (h->upart) h->dfree(h->upart);
+    h->upart = nullptr;
+    TRY(alloc_into(h, h->upart, (size_t)h->Qcr * (h->W / 16) * h->rg.K * h->rg.K));
     CU(cudaMemcpyAsync(h->roots, roots.data(), sizeof(float2) * roots.size(),
                        cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
@@ -614,8 +618,10 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
     const int G = (int)h->gptr.size() - 1;
     for (int g = 0; g < G; ++g) TRY(run_group(h, g, p, on));
     {
+      // the partial sums of this iteration follow its column-pass tiling
+      const size_t nerr = (size_t)h->N * (h->W / (on ? h->tlr.CB : h->tl.CB));
       pty_handle::Mark m(h, PTY_K_REDUCE);
-      CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter + it, h->stream));
+      CU(pty::launch_err_reduce(h->err_part, nerr, inv, h->err_iter + it, h->stream));
     }
     if (on) {
       ++h->adam_t;
@@ -914,10 +920,12 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
   if (t->R && (!pow2(t->R) || W % t->R || M * t->R * L > 256))
     return fail(PTY_EINVAL, "rows per CTA R=%d invalid for W=%d, M=%d", t->R, W, M);
-  if (t->CB && (!pow2(t->CB) || t->CB < 2 || (W / 2) % t->CB || M * t->CB * L > 512))
+  if (t->CB && (!pow2(t->CB) || t->CB < 2 || (W / 2) % t->CB || M * t->CB * L > 384))
     return fail(PTY_EINVAL, "columns per CTA CB=%d invalid for W=%d, M=%d", t->CB, W, M);
   if (t->ppc < 0 || t->ppc > 64) return fail(PTY_EINVAL, "patches per CTA %d", t->ppc);
+  if (t->ppcb < 0 || t->ppcb > 64) return fail(PTY_EINVAL, "column patches per CTA %d", t->ppcb);
   pty::Tiling nt = pty::make_tiling(W, M, false, 512, t->R, t->ppc, t->CB);
+  if (t->ppcb > 0) nt.ppcb = t->ppcb;
   if (nt.smA > 227 * 1024 || nt.smB > 227 * 1024 || nt.smC > 227 * 1024)
     return fail(PTY_EINVAL, "tiling needs too much shared memory");
   const size_t W2 = (size_t)W * W;
@@ -964,6 +972,7 @@ int pty_get_tiling(pty_handle* h, pty_tiling* t) {
   t->ppc = h->tl.ppc;
   t->CB = h->tl.CB;
   t->scratch_bytes = (size_t)h->Qc * h->M * h->W * h->W * sizeof(float2);
+  t->ppcb = h->tl.ppcb;
   return PTY_OK;
 }
 

@@ -297,11 +297,9 @@ static size_t grad_inv_smem(const Tiling& t) {
 cudaError_t set_grad_smem(const Tiling& t) {
   cudaError_t e = cudaSuccess;
   PTY_DISPATCH_W(t.W, {
-    e = cudaFuncSetAttribute(k_grad_rows_fwd<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)t.smA);
+    e = allow_max_smem((const void*)k_grad_rows_fwd<WW>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_grad_rows_inv<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)grad_inv_smem(t));
+      e = allow_max_smem((const void*)k_grad_rows_inv<WW>);
   });
   return e;
 }

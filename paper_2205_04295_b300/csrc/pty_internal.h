@@ -20,12 +20,21 @@ struct Tiling {
   int R;         // rows per CTA, row passes
   int ppc;       // patches per CTA, row passes
   int CB;        // columns per CTA, column pass
+  int ppcb;      // patches per CTA, column pass
   int thrA, thrB, thrC;
   size_t smA, smB, smC, smI;  // dynamic shared memory (bytes)
   int n_pmax;    // CTAs of the probe-apply kernel (= partial maxima)
 };
 
 bool supported_W(int W);
+
+// Largest dynamic shared memory a block may opt in to on the current device.
+// Every kernel's opt-in limit is set to this value: the attribute is global
+// per kernel function, so a limit sized for one tiling would reject another.
+int smem_optin();
+// Let `func` use all dynamic shared memory the device allows beside its own
+// static shared memory.
+cudaError_t allow_max_smem(const void* func);
 
 // Record a failure message for pty_last_error() on this thread; returns code.
 int set_error(int code, const char* fmt, ...);
@@ -103,9 +112,10 @@ cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, 
 cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, int M,
                               int npatch, const float2* tw, float* cval, int* cidx,
                               cudaStream_t s);
+// part: npatch * (W / 16) * K * K complex partial sums of the fine grid
 cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
                          int npatch, const float* cval, const int* cidx, const float2* roots,
-                         float* shift, float* gap, cudaStream_t s);
+                         float2* part, float* shift, float* gap, cudaStream_t s);
 cudaError_t launch_adam(float* pos, float* m, float* v, const float* g, int N, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, float max_step,
                         float ymax, float xmax, cudaStream_t s);

@@ -156,87 +156,106 @@ k_xcorr_rows(const float2* __restrict__ scratch, int npl, int M, int RX,
 }
 
 // ------------------------------------------------------------ updft
-// One CTA per patch: coarse peak, T = X E_c (W x K, shared memory), then
-// c_up = E_r T (K x K), first maximum -> shift.
+// The fine grid is evaluated as c_up = E_r X E_c in two kernels:
+//   updft_part : CTA (row block of RU rows of X, patch): T = X_rows E_c
+//                (RU x K) and the block's share E_r[:, rows] T (K x K),
+//                written as a partial sum;
+//   updft_final: per patch, the partial sums added in block order, |c_up|^2,
+//                first maximum in row-major order -> shift.
+// The phase of every entry is an exact multiple of 2 pi / (U W), read from
+// the root table staged in shared memory.
+constexpr int RU = 16;
+
+PTY_D void coarse_peak(const float* cval, const int* cidx, int lp, int nparts, int W,
+                       int& sy, int& sx, float* rv, int* ri) {
+  float b = -1.f;
+  int bi = 0x7fffffff;
+  for (int e = threadIdx.x; e < nparts; e += blockDim.x)
+    best_merge(b, bi, cval[(size_t)lp * nparts + e], cidx[(size_t)lp * nparts + e]);
+  block_best(b, bi, rv, ri);
+  sy = wrap_shift(bi / W, W);
+  sx = wrap_shift(bi % W, W);
+}
+
 template <int W>
 __global__ void __launch_bounds__(256)
-k_updft(const float2* __restrict__ scratch, int npl, int M, const int* __restrict__ ids,
-        int nparts, const float* __restrict__ cval, const int* __restrict__ cidx,
-        const float2* __restrict__ roots_g, int U, int K, float* __restrict__ shift,
-        float* __restrict__ gap) {
+k_updft_part(const float2* __restrict__ scratch, int npl, int M, int nparts,
+             const float* __restrict__ cval, const int* __restrict__ cidx,
+             const float2* __restrict__ roots_g, int U, int K, float2* __restrict__ part) {
   extern __shared__ float4 smem4[];
   const int UW = U * W;
+  constexpr int XP = W + 1;                  // padded row pitch of the X block
   float2* roots = reinterpret_cast<float2*>(smem4);
-  float2* T = roots + UW;                // [W][K]
-  float2* xrow = T + (size_t)W * K;      // [8 warps][W]
+  float2* Xs = roots + UW;                   // [RU][W + 1]
+  float2* T = Xs + RU * XP;                  // [RU][K]
   __shared__ float rv[32];
   __shared__ int ri[32];
-  __shared__ int s_sy, s_sx;
-  const int lp = blockIdx.x, j = ids[lp];
+  const int lp = blockIdx.y, u0 = blockIdx.x * RU;
   for (int e = threadIdx.x; e < UW; e += blockDim.x) roots[e] = roots_g[e];
-  // coarse peak over the row-block partials
-  {
-    float b = -1.f;
-    int bi = 0x7fffffff;
-    for (int e = threadIdx.x; e < nparts; e += blockDim.x)
-      best_merge(b, bi, cval[(size_t)lp * nparts + e], cidx[(size_t)lp * nparts + e]);
-    block_best(b, bi, rv, ri);
-    if (threadIdx.x == 0) {
-      s_sy = wrap_shift(bi / W, W);
-      s_sx = wrap_shift(bi % W, W);
+  const float2* X = scratch + ((size_t)lp * npl + M) * W * W + (size_t)u0 * W;
+  for (int e = threadIdx.x; e < RU * W; e += blockDim.x) {
+    const int r = e / W, v = e - r * W;
+    Xs[r * XP + v] = X[(size_t)r * W + v];
+  }
+  int sy, sx;
+  coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);  // contains barriers
+  const int half = K / 2;
+  // T[r][k] = sum_v X[u0 + r][v] root[(v_s (U sx + k - half)) mod UW]
+  // lanes of a half-warp: 16 rows sharing one k (one root index per step)
+  for (int q = threadIdx.x; q < RU * K; q += blockDim.x) {
+    const int k = q / RU, r = q - k * RU;
+    const int a = modp((long long)U * sx + k - half, UW);
+    const float2* xr = Xs + r * XP;
+    float2 acc = make_float2(0.f, 0.f);
+    int n = 0;
+    for (int v = 0; v < W / 2; ++v) {
+      acc = cadd(acc, cmul(xr[v], roots[n]));
+      n += a;
+      if (n >= UW) n -= UW;
     }
+    n = modp(-(long long)(W / 2) * a, UW);
+    for (int v = W / 2; v < W; ++v) {
+      acc = cadd(acc, cmul(xr[v], roots[n]));
+      n += a;
+      if (n >= UW) n -= UW;
+    }
+    T[r * K + k] = acc;
   }
   __syncthreads();
-  const int sy = s_sy, sx = s_sx, half = K / 2;
-  const float2* X = scratch + ((size_t)lp * npl + M) * W * W;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarp = blockDim.x >> 5;
-  float2* xr = xrow + warp * W;
-  // T[u][k] = sum_v X[u][v] root[(v_s (U sx + k - half)) mod UW]
-  for (int u = warp; u < W; u += nwarp) {
-    for (int v = lane; v < W; v += 32) xr[v] = X[(size_t)u * W + v];
-    __syncwarp();
-    for (int k = lane; k < K; k += 32) {
-      const int a = modp((long long)U * sx + k - half, UW);
-      float2 acc = make_float2(0.f, 0.f);
-      int n = 0;  // (v * a) mod UW for v = 0, 1, ..
-      for (int v = 0; v < W / 2; ++v) {
-        acc = cadd(acc, cmul(xr[v], roots[n]));
-        n += a;
-        if (n >= UW) n -= UW;
-      }
-      n = modp(-(long long)(W / 2) * a, UW);  // v_s = v - W from v = W/2
-      for (int v = W / 2; v < W; ++v) {
-        acc = cadd(acc, cmul(xr[v], roots[n]));
-        n += a;
-        if (n >= UW) n -= UW;
-      }
-      T[(size_t)u * K + k] = acc;
-    }
-    __syncwarp();
-  }
-  __syncthreads();
-  // c_up[k1][k2] = sum_u root[(u_s (U sy + k1 - half)) mod UW] T[u][k2]
-  float best = -1.f, second = -1.f;
-  int bi = 0x7fffffff;
+  // share of this row block: sum_{r} root[(u_s (U sy + k1 - half)) mod UW] T[r][k2]
+  float2* dst = part + ((size_t)lp * gridDim.x + blockIdx.x) * K * K;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int k1 = e / K, k2 = e - k1 * K;
     const int b = modp((long long)U * sy + k1 - half, UW);
     float2 acc = make_float2(0.f, 0.f);
-    int n = 0;
-    for (int u = 0; u < W / 2; ++u) {
-      acc = cadd(acc, cmul(roots[n], T[(size_t)u * K + k2]));
-      n += b;
-      if (n >= UW) n -= UW;
+    for (int r = 0; r < RU; ++r) {
+      const int u = u0 + r;
+      const int us = u < W / 2 ? u : u - W;
+      acc = cadd(acc, cmul(roots[modp((long long)us * b, UW)], T[r * K + k2]));
     }
-    n = modp(-(long long)(W / 2) * b, UW);
-    for (int u = W / 2; u < W; ++u) {
-      acc = cadd(acc, cmul(roots[n], T[(size_t)u * K + k2]));
-      n += b;
-      if (n >= UW) n -= UW;
-    }
+    dst[e] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_updft_final(const int* __restrict__ ids, int W, int nblocks, int nparts,
+              const float* __restrict__ cval, const int* __restrict__ cidx, int U, int K,
+              const float2* __restrict__ part, float* __restrict__ shift,
+              float* __restrict__ gap) {
+  __shared__ float rv[32];
+  __shared__ int ri[32];
+  const int lp = blockIdx.x, j = ids[lp];
+  int sy, sx;
+  coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);
+  const int half = K / 2;
+  float best = -1.f, second = -1.f;
+  int bi = 0x7fffffff;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < nblocks; ++b)
+      acc = cadd(acc, part[((size_t)lp * nblocks + b) * K * K + e]);  // fixed order
     const float m = cabs2(acc);
-    if (m > best || (m == best && e < bi)) {
+    if (m > best) {
       second = fmaxf(second, best);
       best = m;
       bi = e;
@@ -244,11 +263,10 @@ k_updft(const float2* __restrict__ scratch, int npl, int M, const int* __restric
       second = fmaxf(second, m);
     }
   }
-  // global best, then the best value among all other grid points
   float gb = best;
   int gbi = bi;
   block_best(gb, gbi, rv, ri);
-  float s2 = (bi == gbi) ? second : best;  // this thread's best that is not the winner
+  float s2 = (bi == gbi) ? second : best;  // best of this thread that is not the winner
   __syncthreads();
   {
     int dummy = 0;
@@ -343,21 +361,18 @@ RefGeo make_refgeo(int W, int U) {
     case 192: refgeo_fill<192>(g); break;
     default: refgeo_fill<256>(g); break;
   }
-  g.smU = (size_t)(g.U * W + (size_t)W * g.K + 8 * W) * sizeof(float2);
+  g.smU = (size_t)(g.U * W + RU * (W + 1) + RU * g.K) * sizeof(float2);
   return g;
 }
 
 cudaError_t set_refine_smem(const RefGeo& g) {
   cudaError_t e = cudaSuccess;
   PTY_DISPATCH_W(g.W, {
-    e = cudaFuncSetAttribute(k_xcorr_cols<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)g.smX);
+    e = allow_max_smem((const void*)k_xcorr_cols<WW>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_xcorr_rows<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)g.smR);
+      e = allow_max_smem((const void*)k_xcorr_rows<WW>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_updft<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)g.smU);
+      e = allow_max_smem((const void*)k_updft_part<WW>);
   });
   return e;
 }
@@ -397,16 +412,18 @@ cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, i
 
 cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
                          int npatch, const float* cval, const int* cidx, const float2* roots,
-                         float* shift, float* gap, cudaStream_t s) {
+                         float2* part, float* shift, float* gap, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   const int nparts = g.W / g.RX;
   if (g.U <= 1) {
     k_coarse_only<<<npatch, 128, 0, s>>>(ids, nparts, g.W, cval, cidx, shift, gap);
     return cudaGetLastError();
   }
-  PTY_DISPATCH_W(g.W, (k_updft<WW><<<npatch, 256, g.smU, s>>>(scratch, npl, M, ids, nparts,
-                                                              cval, cidx, roots, g.U, g.K,
-                                                              shift, gap)));
+  const int nblocks = g.W / RU;
+  PTY_DISPATCH_W(g.W, (k_updft_part<WW><<<dim3(nblocks, npatch), 256, g.smU, s>>>(
+                          scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K, part)));
+  k_updft_final<<<npatch, 256, 0, s>>>(ids, g.W, nblocks, nparts, cval, cidx, g.U, g.K, part,
+                                       shift, gap);
   return cudaGetLastError();
 }
 

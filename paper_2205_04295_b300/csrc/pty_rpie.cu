@@ -90,20 +90,31 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
   const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
+  // crop rows of patch lp + 1 are loaded while patch lp is transformed
+  float2 on[G::N1];
+  if (p0 < p1 && act && lane < G::N2) {
+    const int2 cc = corners[ids[p0]];
+    const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) on[n1] = orow[G::N2 * n1 + lane];
+  }
   for (int lp = p0; lp < p1; ++lp) {
-    const int j = ids[lp];
-    const int2 cc = corners[j];
     float omax = 0.f;
     if (act && lane < G::N2) {
-      const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
       const float2* prow = Prow + (k * R + r) * W;
       float2 v[G::N1];
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
-        const float2 o = orow[c];
+        const float2 o = on[n1];
         v[n1] = k < M ? cmul(prow[c], o) : o;
         omax = fmaxf(omax, cabs2(o));
+      }
+      if (lp + 1 < p1) {
+        const int2 cn = corners[ids[lp + 1]];
+        const float2* orow = O + (size_t)(cn.x + r0 + r) * Hx + cn.y;
+#pragma unroll
+        for (int n1 = 0; n1 < G::N1; ++n1) on[n1] = orow[G::N2 * n1 + lane];
       }
       fwd_step1<W>(v, lane, tw, lbuf);
     }
@@ -138,95 +149,107 @@ template <int W, bool GRAD>
 PTY_D void cols_body(float2* __restrict__ scratch, int M, int CB,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part, int npl, int xo, int bx, int by) {
+       float* __restrict__ err_part, int npl, int xo, int ppcb, int npatch, int bx, int by) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* tbuf = tw + W;
   float* Sb = reinterpret_cast<float*>(tbuf + (M + xo) * CB * G::LP);
+  float* Isq = Sb + M * CB * W;  // sqrt of the counts of this column block
   __shared__ float red[32];
 
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
-  const int lp = by, c0 = bx * CB;
+  const int c0 = bx * CB;
   const int c = threadIdx.x % CB, rest = threadIdx.x / CB;
   const int lane = rest % G::L, k = rest / G::L;
   // k < M: the modes; k == M (with xo): the crop, forward transform only
   const bool act = k < M + xo;
   const bool mode = k < M;
-  const int j = ids[lp];
-  float2* col = scratch + ((size_t)lp * npl + (act ? k : 0)) * W * W + c0 + c;
   float2* lbuf = tbuf + ((act ? k : 0) * CB + c) * G::LP;
+  const int p0 = by * ppcb, p1 = min(npatch, p0 + ppcb);
   __syncthreads();
-
-  float2 v[G::N1];
-  if (act && lane < G::N2) {
+  for (int lp = p0; lp < p1; ++lp) {
+    const int j = ids[lp];
+    float2* col = scratch + ((size_t)lp * npl + (act ? k : 0)) * W * W + c0 + c;
+    float2 v[G::N1];
+    if (act && lane < G::N2) {
 #pragma unroll
-    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = col[(size_t)(G::N2 * n1 + lane) * W];
-    fwd_step1<W>(v, lane, tw, lbuf);
-  }
-  __syncthreads();
-  float2 z[G::N2];
-  if (act && lane < G::N1) {
-    fwd_step3<W>(z, lane, lbuf);
-    if (mode) {
-#pragma unroll
-      for (int k2 = 0; k2 < G::N2; ++k2)
-        Sb[(k * W + lane + G::N1 * k2) * CB + c] = cabs2(z[k2]);
-    } else {
-#pragma unroll
-      for (int k2 = 0; k2 < G::N2; ++k2) col[(size_t)(lane + G::N1 * k2) * W] = z[k2];
+      for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = col[(size_t)(G::N2 * n1 + lane) * W];
     }
-  }
-  __syncthreads();
-  // constraint factor once per detector pixel (u, c): S = sum_k |Psi_k|^2 in a
-  // fixed mode order, f = sqrt(I) / (sqrt(S) + eps) folded with both 1/W
-  // normalisations; stored over mode 0's |Psi|^2.
-  float e = 0.f;
-  {
-    const float f2 = inv_w * inv_w;
-    const uint16_t* Ij = I + (size_t)j * W * W;
-    for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
-      const int u = el / CB, cl = el - u * CB;
-      float s = 0.f;
-      for (int kk = 0; kk < M; ++kk) s += Sb[(kk * W + u) * CB + cl];
-      const float sI = sqrtf((float)__ldg(Ij + (size_t)((u + W / 2) % W) * W + (c0 + cl + W / 2) % W));
-      if (!GRAD) {
-        const float a = sqrtf(s) * inv_w;
-        const float d = a - sI;
-        e = fmaf(d, d, e);
-        Sb[u * CB + cl] = sI / (a + eps) * f2;
-      } else {
-        const float a = sqrtf(fmaf(s, f2, eps));
-        const float d = a - sI;
-        e = fmaf(d, d, e);
-        Sb[u * CB + cl] = 2.f * (1.f - sI / a) * f2;
+    {
+      // the counts are requested together with the columns: one round trip
+      const uint16_t* Ij = I + (size_t)j * W * W;
+      for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
+        const int u = el / CB, cl = el - u * CB;
+        Isq[el] = sqrtf((float)__ldg(Ij + (size_t)((u + W / 2) % W) * W + (c0 + cl + W / 2) % W));
       }
     }
-  }
-  __syncthreads();
-  if (mode && lane < G::N1) {
+    if (act && lane < G::N2) fwd_step1<W>(v, lane, tw, lbuf);
+    __syncthreads();
+    float2 z[G::N2];
+    if (act && lane < G::N1) {
+      fwd_step3<W>(z, lane, lbuf);
+      if (mode) {
 #pragma unroll
-    for (int k2 = 0; k2 < G::N2; ++k2)
-      z[k2] = cscale(z[k2], Sb[(lane + G::N1 * k2) * CB + c]);
-    inv_stepA<W>(z, lane, tw, lbuf);
-  }
-  __syncthreads();
-  if (mode && lane < G::N2) {
-    inv_stepB<W>(v, lane, lbuf);
+        for (int k2 = 0; k2 < G::N2; ++k2)
+          Sb[(k * W + lane + G::N1 * k2) * CB + c] = cabs2(z[k2]);
+      } else {
 #pragma unroll
-    for (int n1 = 0; n1 < G::N1; ++n1) col[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
+        for (int k2 = 0; k2 < G::N2; ++k2) col[(size_t)(lane + G::N1 * k2) * W] = z[k2];
+      }
+    }
+    __syncthreads();
+    // constraint factor once per detector pixel (u, c): S = sum_k |Psi_k|^2 in a
+    // fixed mode order, f = sqrt(I) / (sqrt(S) + eps) folded with both 1/W
+    // normalisations; stored over mode 0's |Psi|^2.
+    float e = 0.f;
+    {
+      const float f2 = inv_w * inv_w;
+      for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
+        const int u = el / CB, cl = el - u * CB;
+        float s = 0.f;
+        for (int kk = 0; kk < M; ++kk) s += Sb[(kk * W + u) * CB + cl];
+        const float sI = Isq[el];
+        if (!GRAD) {
+          const float a = sqrtf(s) * inv_w;
+          const float d = a - sI;
+          e = fmaf(d, d, e);
+          Sb[u * CB + cl] = sI / (a + eps) * f2;
+        } else {
+          const float a = sqrtf(fmaf(s, f2, eps));
+          const float d = a - sI;
+          e = fmaf(d, d, e);
+          Sb[u * CB + cl] = 2.f * (1.f - sI / a) * f2;
+        }
+      }
+    }
+    __syncthreads();
+    if (mode && lane < G::N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2)
+        z[k2] = cscale(z[k2], Sb[(lane + G::N1 * k2) * CB + c]);
+      inv_stepA<W>(z, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (mode && lane < G::N2) {
+      inv_stepB<W>(v, lane, lbuf);
+#pragma unroll
+      for (int n1 = 0; n1 < G::N1; ++n1) col[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
+    }
+    e = block_sum(e, red);  // its barriers also guard lbuf and Sb reuse
+    if (threadIdx.x == 0) err_part[(size_t)j * (W / CB) + bx] = e;
   }
-  e = block_sum(e, red);
-  if (threadIdx.x == 0) err_part[(size_t)j * (W / CB) + bx] = e;
 }
 
+
 template <int W, bool GRAD>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(384)
 k_cols(float2* __restrict__ scratch, int M, int CB,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part, int npl, int xo) {
-  cols_body<W, GRAD>(scratch, M, CB, I, ids, tw_g, inv_w, eps, err_part, npl, xo, blockIdx.x, blockIdx.y);
+       float* __restrict__ err_part, int npl, int xo, int ppcb, int npatch) {
+  cols_body<W, GRAD>(scratch, M, CB, I, ids, tw_g, inv_w, eps, err_part, npl, xo, ppcb, npatch,
+                     blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- pass C
@@ -246,9 +269,10 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   float2* Prow = tw + W;
   float2* tbuf = Prow + M * R * W;  // transpose buffer, then D conj(P) terms
   float2* num = tbuf + TB;
-  float2* onew = num + M * R * W;   // refined crop rows (refine only)
-  float* Pint = reinterpret_cast<float*>(onew + (refine ? R * W : 0));
-  float* den = Pint + R * W;
+  float2* ostash = num + M * R * W;  // the crop rows of the current patch
+  float2* onew = ostash + R * W;     // refined crop rows (refine only)
+  float* invd = reinterpret_cast<float*>(onew + (refine ? R * W : 0));  // alpha_O / denominator
+  float* den = invd + R * W;
   __shared__ float s_pmax, s_omax;
 
   const int r0 = bx * R;
@@ -266,14 +290,17 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     if (threadIdx.x == 0) s_pmax = m;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < M; ++k) s += cabs2(Prow[k * R * W + e]);
-    Pint[e] = s;
-    den[e] = 0.f;
+  {
+    const float pmax = s_pmax;
+    const float gden = a.gamma * pmax + a.reg_eps * pmax;
+    for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+      float s = 0.f;
+      for (int k = 0; k < M; ++k) s += cabs2(Prow[k * R * W + e]);
+      const float dn = fmaf(1.f - a.gamma, s, gden);
+      invd[e] = dn > 0.f ? a.alpha_O / dn : 0.f;  // a zero denominator has a zero numerator
+      den[e] = 0.f;
+    }
   }
-  const float pmax = s_pmax;
-  const float gden = a.gamma * pmax + a.reg_eps * pmax;
 
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
   const bool act = line < M * R;
@@ -282,34 +309,43 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
   float osum_local = 0.f;
   for (int lp = p0; lp < p1; ++lp) {
-    const int j = ids[lp];
-    const int2 cc = corners[j];
+    const int2 cc = corners[ids[lp]];
+    // the far-field rows and the crop rows are requested together: one
+    // global round trip per patch
+    float2 z[G::N2], oc[G::N1];
+    if (act && lane < G::N1) {
+      const float2* src = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
+    }
+    if (act && lane < G::N2) {
+      const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
+#pragma unroll
+      for (int n1 = 0; n1 < G::N1; ++n1) oc[n1] = orow[G::N2 * n1 + lane];
+    }
     if (threadIdx.x < 32) {
       float m = 0.f;
       for (int i = threadIdx.x; i < nrb; i += 32) m = fmaxf(m, omax_part[(size_t)lp * nrb + i]);
       m = warp_max(m);
       if (threadIdx.x == 0) s_omax = m;
     }
-    if (act && lane < G::N1) {
-      const float2* src = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
-      float2 z[G::N2];
+    if (act && lane < G::N1) inv_stepA<W>(z, lane, tw, lbuf);
+    if (act && k == 0 && lane < G::N2) {
 #pragma unroll
-      for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
-      inv_stepA<W>(z, lane, tw, lbuf);
+      for (int n1 = 0; n1 < G::N1; ++n1) ostash[r * W + G::N2 * n1 + lane] = oc[n1];
     }
     __syncthreads();
     float2 v[G::N1];
     if (act && lane < G::N2) inv_stepB<W>(v, lane, lbuf);
     __syncthreads();  // tbuf is reused below for the D conj(P) terms
     if (act && lane < G::N2) {
-      const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
       float2* T = tbuf + (k * R + r) * W;
       float2* nm = num + (k * R + r) * W;
       const float2* prow = Prow + (k * R + r) * W;
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
-        const float2 o = orow[c];
+        const float2 o = oc[n1];
         const float2 Pk = prow[c];
         const float2 D = csub(v[n1], cmul(Pk, o));
         T[c] = cmulc(D, Pk);
@@ -320,15 +356,13 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     const float om = s_omax;
     for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
       const int rr = e / W, c = e - rr * W;
-      float2* op = O + (size_t)(cc.x + r0 + rr) * Hx + cc.y + c;
-      const float2 o = *op;
+      const float2 o = ostash[e];
       float2 s = make_float2(0.f, 0.f);
       for (int kk = 0; kk < M; ++kk) s = cadd(s, tbuf[(kk * R + rr) * W + c]);
-      const float dn = fmaf(1.f - a.gamma, Pint[e], gden);
-      const float sc = dn > 0.f ? a.alpha_O / dn : 0.f;  // zero numerator too
-      const float2 on = make_float2(fmaf(sc, s.x, o.x), fmaf(sc, s.y, o.y));
-      *op = on;
-      if (refine) onew[e] = on;
+      const float sc = invd[e];
+      const float2 onw = make_float2(fmaf(sc, s.x, o.x), fmaf(sc, s.y, o.y));
+      O[(size_t)(cc.x + r0 + rr) * Hx + cc.y + c] = onw;
+      if (refine) onew[e] = onw;
       den[e] += fmaf(1.f - a.beta, cabs2(o), a.beta * om);
     }
     osum_local += om;
@@ -343,11 +377,11 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
       }
       __syncthreads();
       if (line < R && lane < G::N1) {
-        float2 z[G::N2];
-        fwd_step3<W>(z, lane, tbuf + line * G::LP);
+        float2 zz[G::N2];
+        fwd_step3<W>(zz, lane, tbuf + line * G::LP);
         float2* dst = scratch + (((size_t)lp * npl + M + 1) * W + r0 + line) * W;
 #pragma unroll
-        for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
+        for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = zz[k2];
       }
       __syncthreads();
     }
@@ -603,6 +637,24 @@ template <int W> void geo(int& L, int& LP) {
 
 }  // namespace
 
+int smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 227 * 1024;
+  }
+  return v;
+}
+
+cudaError_t allow_max_smem(const void* func) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_optin() - (int)fa.sharedSizeBytes);
+}
+
 int lanes_per_line(int W) {
   int L = 16, LP = 0;
   switch (W) {
@@ -631,7 +683,7 @@ bool supported_W(int W) {
     default: return cudaErrorInvalidValue;                   \
   }
 
-Tiling make_tiling(int W, int M, bool refine, int max_threads_b, int R_req, int ppc_req,
+Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, int ppc_req,
                    int CB_req) {
   Tiling t{};
   t.W = W;
@@ -649,12 +701,14 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b, int R_req, int 
     default: geo<256>(L, LP); break;
   }
   const int MA = M + t.xo;  // lines per row in pass A, columns-groups in pass B
+  const int max_threads_b = std::min(max_threads_b_req, 384);
   int R = pow2_floor(std::max(1, 256 / (MA * L)));
   R = std::min(R, 16);
   while (W % R) R /= 2;
   if (R_req > 0) R = R_req;
   t.R = R;
   t.ppc = ppc_req > 0 ? ppc_req : 4;
+  t.ppcb = 2;
   int CB = pow2_floor(std::max(1, max_threads_b / (MA * L)));
   CB = std::max(2, std::min(16, CB));  // MA * CB * L <= max_threads_b threads
   while ((W / 2) % CB) CB /= 2;
@@ -664,10 +718,10 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b, int R_req, int 
   t.thrC = round32(M * R * L);
   t.thrB = round32(MA * CB * L);
   t.smA = (size_t)(W + M * R * W + MA * R * LP) * sizeof(float2);
-  t.smB = (size_t)(W + MA * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
+  t.smB = (size_t)(W + MA * CB * LP) * sizeof(float2) + (size_t)(M + 1) * CB * W * sizeof(float);
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
-  t.smC = (size_t)(W + M * R * W + TB + M * R * W + (refine ? R * W : 0)) * sizeof(float2) +
+  t.smC = (size_t)(W + M * R * W + TB + M * R * W + R * W + (refine ? R * W : 0)) * sizeof(float2) +
           (size_t)2 * R * W * sizeof(float);
   t.n_pmax = std::max(1, std::min(1024, W * W / 256));
   return t;
@@ -676,15 +730,15 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b, int R_req, int 
 cudaError_t set_smem_limits(const Tiling& t) {
   cudaError_t e = cudaSuccess;
   PTY_DISPATCH_W(t.W, {
-    e = cudaFuncSetAttribute(k_rows_fwd<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smA);
+    e = allow_max_smem((const void*)k_rows_fwd<WW>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_cols<WW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smB);
+      e = allow_max_smem((const void*)k_cols<WW, false>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_cols<WW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smB);
+      e = allow_max_smem((const void*)k_cols<WW, true>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_rows_inv<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smC);
+      e = allow_max_smem((const void*)k_rows_inv<WW>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_cols_intensity<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smI);
+      e = allow_max_smem((const void*)k_cols_intensity<WW>);
   });
   return e;
 }
@@ -727,9 +781,10 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
                         float eps, float* err_part, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
-  dim3 grid(t.W / t.CB, npatch);
+  dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   PTY_DISPATCH_W(t.W, (k_cols<WW, false><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, t.CB, I, ids, tw, inv_w, eps, err_part, t.npl, t.xo)));
+                          scratch, t.M, t.CB, I, ids, tw, inv_w, eps, err_part, t.npl, t.xo,
+                          t.ppcb, npatch)));
   return cudaGetLastError();
 }
 
@@ -737,9 +792,10 @@ cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I
                              const int* ids, int npatch, const float2* tw, float inv_w,
                              float delta, float* loss_part, int npl, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
-  dim3 grid(t.W / t.CB, npatch);
+  dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   PTY_DISPATCH_W(t.W, (k_cols<WW, true><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, t.CB, I, ids, tw, inv_w, delta, loss_part, npl, 0)));
+                          scratch, t.M, t.CB, I, ids, tw, inv_w, delta, loss_part, npl, 0,
+                          t.ppcb, npatch)));
   return cudaGetLastError();
 }
 
@@ -857,7 +913,7 @@ __device__ __noinline__ void batch_task(const BatchProb& pb, const BatchTask& tk
     case BT_COLS:
       for (int bx = tk.x0; bx < tk.x1; ++bx) {
         cols_body<W, false>(pb.scratch, pb.M, pb.CB, pb.I, ids, pb.tw, pb.inv_w, pb.a.eps,
-                            pb.err_part, pb.M, 0, bx, tk.y);
+                            pb.err_part, pb.M, 0, 1, tk.npatch, bx, tk.y);
         __syncthreads();
       }
       break;
@@ -942,7 +998,7 @@ k_batch(const BatchProb* __restrict__ probs, const BatchTask* __restrict__ tasks
 size_t batch_smem(const Tiling& t) { return std::max(std::max(t.smA, t.smB), t.smC); }
 
 cudaError_t batch_grid(size_t smem, int* ctas) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void*)k_batch);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

@@ -60,7 +60,8 @@ class Stats(ctypes.Structure):
 
 
 class Tiling(ctypes.Structure):
-    _fields_ = [("R", c_int), ("ppc", c_int), ("CB", c_int), ("scratch_bytes", c_size_t)]
+    _fields_ = [("R", c_int), ("ppc", c_int), ("CB", c_int), ("scratch_bytes", c_size_t),
+                ("ppcb", c_int)]
 
 
 class BatchSchedule(ctypes.Structure):
@@ -348,13 +349,14 @@ class Problem:
                                   out.data_ptr(), gO.data_ptr(), gP.data_ptr(), gpos.data_ptr()))
         return out, gO, gP, gpos
 
-    def set_tiling(self, R=0, ppc=0, CB=0, scratch_bytes=0):
-        check(lib().pty_set_tiling(self.h, ctypes.byref(Tiling(R, ppc, CB, scratch_bytes))))
+    def set_tiling(self, R=0, ppc=0, CB=0, scratch_bytes=0, ppcb=0):
+        check(lib().pty_set_tiling(self.h, ctypes.byref(Tiling(R, ppc, CB, scratch_bytes, ppcb))))
 
     def tiling(self):
         t = Tiling()
         check(lib().pty_get_tiling(self.h, ctypes.byref(t)))
-        return {"R": t.R, "ppc": t.ppc, "CB": t.CB, "scratch_bytes": int(t.scratch_bytes)}
+        return {"R": t.R, "ppc": t.ppc, "CB": t.CB, "scratch_bytes": int(t.scratch_bytes),
+                "ppcb": t.ppcb}
 
     def profile(self, mode):
         check(lib().pty_profile(self.h, int(mode)))

@@ -226,7 +226,24 @@ def test_tiling_overrides_keep_parity_and_bad_ones_are_rejected():
         prob.run(2)
         assert rel_l2(prob.object(False), ref.object(False)) <= 1e-6
         assert rel_l2(prob.probe(False), ref.probe(False)) <= 1e-6
-    for bad in ((3, 0, 0), (32, 0, 0), (0, 0, 3), (0, 0, 128), (0, -1, 0)):
+    for bad in ((3, 0, 0), (32, 0, 0), (0, 0, 3), (0, 0, 128), (0, 0, 16), (0, -1, 0)):
         with pytest.raises(pty.PtyError) as e:
             ref.set_tiling(*bad)
         assert e.value.code == pty.PTY_EINVAL
+
+
+def test_unfused_comparison_form_computes_the_same_iteration():
+    """The torch/cuFFT comparison form must compute what the library computes,
+    so that timing the two compares like with like."""
+    import torch
+    from paper_2205_04295_b300.unfused import UnfusedRPIE
+    wl = synth.tiny(W=64, M=3, ny=5, nx=5, step=12.0, seed=61, photons=1e6)
+    d = build(wl)
+    prob = gpu_problem(wl, d)
+    prob.run(1)
+    u = UnfusedRPIE(torch.from_numpy(d["O0"]).cuda(), torch.from_numpy(d["P0"]).cuda(),
+                    torch.from_numpy(d["I"].astype(np.int32)).cuda(),
+                    torch.from_numpy(d["pos"]).cuda(), wl.W, max_chunk=4)
+    u.iteration()
+    assert rel_l2(u.O.cpu().numpy(), prob.object(False)) <= 1e-5
+    assert rel_l2(u.P.cpu().numpy(), prob.probe(False)) <= 1e-5
