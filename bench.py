@@ -120,7 +120,11 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend=None):
+    """Rank, world size and local rank from the launcher's environment; for a
+    world > 1 the process group (nccl on GPUs, gloo otherwise).  Replicas
+    only: the group carries the barrier and the max-over-ranks of the timing,
+    never data of the reconstruction."""
     import torch
     import torch.distributed as dist
     rank = int(os.environ.get("RANK", "0"))
@@ -128,9 +132,11 @@ def dist_setup(n_gpus):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        if torch.cuda.is_available():
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
             torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -145,9 +151,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(units_per_rank, seconds_per_rank, world):
+    """Whole-job throughput of `world` independent replicas: all units over
+    the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / max_over_ranks(seconds_per_rank, world)
 
 
 # ------------------------------------------------------------------ oracle
@@ -260,8 +273,8 @@ def run_ours(args, wl, rank, world, local):
     ms = start.elapsed_time(stop)
     barrier(world)
     st = prob.stats(reset=True)
+    value = replica_rate(wl.N * args.steps, ms / 1e3, world)
     ms = max_over_ranks(ms, world)
-    value = world * wl.N * args.steps / (ms / 1e3)
     launches = sum(st["launches"].values())
 
     # ---- the same step with XCORR_A registration and the Adam position step on
