@@ -181,7 +181,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M, int CB,
       const uint16_t* Ij = I + (size_t)j * W * W;
       for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
         const int u = el / CB, cl = el - u * CB;
-        Isq[el] = sqrtf((float)__ldg(Ij + (size_t)((u + W / 2) % W) * W + (c0 + cl + W / 2) % W));
+        Isq[el] = sqrtf((float)__ldcs(Ij + (size_t)((u + W / 2) % W) * W + (c0 + cl + W / 2) % W));
       }
     }
     if (act && lane < G::N2) fwd_step1<W>(v, lane, tw, lbuf);
@@ -312,16 +312,16 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     const int2 cc = corners[ids[lp]];
     // the far-field rows and the crop rows are requested together: one
     // global round trip per patch
-    float2 z[G::N2], oc[G::N1];
+    float2 z[G::N2];
     if (act && lane < G::N1) {
       const float2* src = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
     }
-    if (act && lane < G::N2) {
+    if (act && k == 0 && lane < G::N2) {
       const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
 #pragma unroll
-      for (int n1 = 0; n1 < G::N1; ++n1) oc[n1] = orow[G::N2 * n1 + lane];
+      for (int n1 = 0; n1 < G::N1; ++n1) ostash[r * W + G::N2 * n1 + lane] = orow[G::N2 * n1 + lane];
     }
     if (threadIdx.x < 32) {
       float m = 0.f;
@@ -330,10 +330,6 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
       if (threadIdx.x == 0) s_omax = m;
     }
     if (act && lane < G::N1) inv_stepA<W>(z, lane, tw, lbuf);
-    if (act && k == 0 && lane < G::N2) {
-#pragma unroll
-      for (int n1 = 0; n1 < G::N1; ++n1) ostash[r * W + G::N2 * n1 + lane] = oc[n1];
-    }
     __syncthreads();
     float2 v[G::N1];
     if (act && lane < G::N2) inv_stepB<W>(v, lane, lbuf);
@@ -345,7 +341,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
-        const float2 o = oc[n1];
+        const float2 o = ostash[r * W + c];
         const float2 Pk = prow[c];
         const float2 D = csub(v[n1], cmul(Pk, o));
         T[c] = cmulc(D, Pk);
@@ -402,7 +398,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
 }
 
 template <int W>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
            int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
@@ -757,9 +753,9 @@ cudaError_t launch_rows_fwd(const Tiling& t, const float2* O, int Hx, const floa
                             cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
-  PTY_DISPATCH_W(t.W, (k_rows_fwd<WW><<<grid, t.thrA, t.smA, s>>>(
-                          O, Hx, P, t.M, t.R, t.ppc, ids, corners, npatch, tw,
-                          scratch, omax_part, t.npl, t.xo)));
+  PTY_DISPATCH_W(t.W, (k_rows_fwd<WW><<<grid, t.thrA, t.smA, s>>>(O, Hx, P,
+                                    t.M, t.R, t.ppc, ids, corners, npatch, tw, scratch,
+                                    omax_part, t.npl, t.xo)));
   return cudaGetLastError();
 }
 
@@ -782,9 +778,9 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         float eps, float* err_part, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
-  PTY_DISPATCH_W(t.W, (k_cols<WW, false><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, t.CB, I, ids, tw, inv_w, eps, err_part, t.npl, t.xo,
-                          t.ppcb, npatch)));
+  PTY_DISPATCH_W(t.W, (k_cols<WW, false><<<grid, t.thrB, t.smB, s>>>(scratch,
+                                    t.M, t.CB, I, ids, tw, inv_w, eps, err_part, t.npl, t.xo,
+                                    t.ppcb, npatch)));
   return cudaGetLastError();
 }
 
@@ -807,10 +803,10 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             float* osum, int accumulate, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
-  PTY_DISPATCH_W(t.W, (k_rows_inv<WW><<<grid, t.thrC, t.smC, s>>>(
-                          O, Hx, P, t.M, t.R, t.ppc, ids, corners, npatch, scratch,
-                          omax_part, pmax_part, t.n_pmax, tw, a, pnum, pden, osum,
-                          accumulate, t.npl, t.refine)));
+  PTY_DISPATCH_W(t.W, (k_rows_inv<WW><<<grid, t.thrC, t.smC, s>>>(O, Hx, P,
+                                    t.M, t.R, t.ppc, ids, corners, npatch, scratch, omax_part,
+                                    pmax_part, t.n_pmax, tw, a, pnum, pden, osum, accumulate,
+                                    t.npl, t.refine)));
   return cudaGetLastError();
 }
 
@@ -941,7 +937,7 @@ __device__ __noinline__ void batch_task(const BatchProb& pb, const BatchTask& tk
 __global__ void __launch_bounds__(256)
 k_batch(const BatchProb* __restrict__ probs, const BatchTask* __restrict__ tasks, int ntask,
         unsigned* next, unsigned* done, int* error, unsigned long long timeout_ns) {
-  __shared__ int s_t, s_stop;
+  __shared__ int s_stop;
   __shared__ BatchProb s_pb;  // descriptor and task live in shared memory, not registers
   __shared__ BatchTask s_tk;
   for (;;) {
@@ -967,7 +963,6 @@ k_batch(const BatchProb* __restrict__ probs, const BatchTask* __restrict__ tasks
         }
         __threadfence();
       }
-      s_t = t;
       s_stop = stop;
       if (!stop) {
         s_tk = tasks[t];
