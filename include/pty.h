@@ -165,7 +165,8 @@ int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t,
 /* Launch geometry of the plain M-rPIE passes, for tuning (0 = default):
  * R rows per CTA of the row passes (M * R * lanes <= 256 threads), ppc
  * patches per CTA of the row passes, CB columns per CTA of the column pass
- * (M * CB * lanes <= 384 threads), scratch_bytes the far-field chunk budget,
+ * (2, 4, 8 or 16, dividing W/2; M * CB * lanes <= 384 threads), scratch_bytes
+ * the far-field chunk budget,
  * ppcb patches per CTA of the column pass.  Results do not depend on the
  * tiling except through the summation order of the probe sums.  The
  * project's autotuner (paper_2205_04295_b300/autotune.py) searches these. */

@@ -2,6 +2,7 @@
 
 Usage: python -m paper_2205_04295_b300.build [--force]
 """
+import concurrent.futures
 import glob
 import os
 import subprocess
@@ -14,6 +15,7 @@ SOURCES = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu")))
 HEADERS = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + glob.glob(os.path.join(HERE, "csrc", "*.h"))
                  + glob.glob(os.path.join(ROOT, "include", "*.h")))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+RDC = {"pty_batch.cu"}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "-Xptxas", "-warn-spills"]
 
@@ -37,15 +39,25 @@ def build(force=False, verbose=False):
         return LIB
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    objs = []
+    cmds, objs = [], []
     for src in SOURCES:
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
-        cmd = [nvcc(), *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-dc", src, "-o", obj]
+        # whole-program compilation per file (no file calls another's device
+        # code): relocatable device code would give every kernel of a file
+        # the static shared memory of all of that file's functions.  The
+        # persistent batched kernel alone is relocatable, so that its
+        # per-pass task functions keep their own register allocations.
+        mode = "-dc" if os.path.basename(src) in RDC else "-c"
+        cmd = [nvcc(), *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), mode, src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
             print(" ".join(cmd))
-        subprocess.run(cmd, check=True)
+        cmds.append(cmd)
         objs.append(obj)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+        for r in ex.map(lambda c: subprocess.run(c), cmds):
+            if r.returncode:
+                raise subprocess.CalledProcessError(r.returncode, r.args)
     tmp = LIB + ".tmp"
     subprocess.run([nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp], check=True)
     os.replace(tmp, LIB)

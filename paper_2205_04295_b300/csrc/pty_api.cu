@@ -920,7 +920,7 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
   if (t->R && (!pow2(t->R) || W % t->R || M * t->R * L > 256))
     return fail(PTY_EINVAL, "rows per CTA R=%d invalid for W=%d, M=%d", t->R, W, M);
-  if (t->CB && (!pow2(t->CB) || t->CB < 2 || (W / 2) % t->CB || M * t->CB * L > 384))
+  if (t->CB && (!pow2(t->CB) || t->CB < 2 || t->CB > 16 || (W / 2) % t->CB || M * t->CB * L > 384))
     return fail(PTY_EINVAL, "columns per CTA CB=%d invalid for W=%d, M=%d", t->CB, W, M);
   if (t->ppc < 0 || t->ppc > 64) return fail(PTY_EINVAL, "patches per CTA %d", t->ppc);
   if (t->ppcb < 0 || t->ppcb > 64) return fail(PTY_EINVAL, "column patches per CTA %d", t->ppcb);

@@ -1,0 +1,514 @@
+// Device bodies of the M-rPIE passes, shared by the per-pass kernels and the
+// persistent batched kernel.  Equations are those of the M-rPIE section of
+// Guzzi et al. (arXiv 2205.04295): exit waves (Eq. 1, per mode as in Eq. 4),
+// far-field propagation (Eq. 2, unitary DFT), the mixed-state modulus
+// constraint (Eq. 7), the object update (Eq. 6) and the probe update (Eq. 5).
+//
+// Pass A  rows_fwd : per (row block, patches): psi_p = P_p o_j for every mode,
+//                    forward row DFTs, rows written to the far-field scratch;
+//                    also the row block's max |o_j|^2.
+// Pass B  cols     : per (column block, patch): forward column DFTs of every
+//                    mode, S = sum_p |Psi_p|^2, Psi'_p = sqrt(I)/(sqrt(S)+eps)
+//                    Psi_p, error partial sum, inverse column DFTs.
+// Pass C  rows_inv : per (row block, patches): inverse row DFTs -> psi'_p,
+//                    D_p = psi'_p - psi_p, object update written in place
+//                    (boxes of a group are disjoint), probe numerator /
+//                    denominator partial sums kept per CTA column.
+// probe_apply      : P_p += alpha_P sum(num_p) / sum(den), fixed-order sums
+//                    over the CTA-column partials; new max_r sum_p |P_p|^2.
+//
+// All reductions run in a fixed order, so results are bitwise repeatable.
+#pragma once
+#include "pty_copy.cuh"
+#include "pty_fft.cuh"
+#include "pty_internal.h"
+
+namespace pty {
+
+namespace {
+
+
+PTY_D float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+PTY_D float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Block-wide maximum; every thread gets the result.  Contains barriers.
+PTY_D float block_max(float v, float* red) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int i = 0; i < nw; ++i) t = fmaxf(t, red[i]);
+  return t;
+}
+
+// ---------------------------------------------------------------- pass A
+template <int W>
+PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
+           int M, int R, int ppc, const int* __restrict__ ids,
+           const int2* __restrict__ corners, int npatch,
+           const float2* __restrict__ tw_g, float2* __restrict__ scratch,
+           float* __restrict__ omax_part, int npl, int xo, int bx, int by) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* Prow = tw + W;
+  float2* tbuf = Prow + M * R * W;
+  __shared__ float red[32];
+
+  const int r0 = bx * R;
+  const int nrb = W / R;
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
+    const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
+    Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
+  }
+  __syncthreads();
+
+  // lines: (mode k, row r) for k < M, and with xo the crop itself as plane M
+  const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
+  const bool act = line < (M + xo) * R;
+  const int k = act ? line / R : 0, r = act ? line - k * R : 0;
+  float2* lbuf = tbuf + line * G::LP;
+  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
+  // crop rows of patch lp + 1 are loaded while patch lp is transformed
+  float2 on[G::N1];
+  if (p0 < p1 && act && lane < G::N2) {
+    const int2 cc = corners[ids[p0]];
+    const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) on[n1] = orow[G::N2 * n1 + lane];
+  }
+  for (int lp = p0; lp < p1; ++lp) {
+    float omax = 0.f;
+    if (act && lane < G::N2) {
+      const float2* prow = Prow + (k * R + r) * W;
+      float2 v[G::N1];
+#pragma unroll
+      for (int n1 = 0; n1 < G::N1; ++n1) {
+        const int c = G::N2 * n1 + lane;
+        const float2 o = on[n1];
+        v[n1] = k < M ? cmul(prow[c], o) : o;
+        omax = fmaxf(omax, cabs2(o));
+      }
+      if (lp + 1 < p1) {
+        const int2 cn = corners[ids[lp + 1]];
+        const float2* orow = O + (size_t)(cn.x + r0 + r) * Hx + cn.y;
+#pragma unroll
+        for (int n1 = 0; n1 < G::N1; ++n1) on[n1] = orow[G::N2 * n1 + lane];
+      }
+      fwd_step1<W>(v, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (act && lane < G::N1) {
+      float2 z[G::N2];
+      fwd_step3<W>(z, lane, lbuf);
+      float2* dst = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
+    }
+    omax = block_max(omax, red);  // its barriers also guard lbuf reuse
+    if (threadIdx.x == 0) omax_part[(size_t)lp * nrb + bx] = omax;
+  }
+}
+
+// ---------------------------------------------------------------- pass B
+// Request (cp.async) the column block [c0, c0 + CB) of the MA planes of patch
+// slot lp into `stage` ([plane][row][column]) and the block's counts into
+// `cnt` ([row][column], rows and columns fftshifted, DC at the centre of the
+// stored pattern).  CB is even, so every segment is 16-byte aligned.
+template <int W, int CB>
+PTY_D void cols_stage(const float2* scratch, const uint16_t* I, int j, int lp, int npl, int MA,
+                      int c0, float2* stage, uint16_t* cnt) {
+  const int cpr = CB / 2;  // 16-byte chunks per row segment
+  const int nch = MA * W * cpr;
+  for (int i = threadIdx.x; i < nch; i += blockDim.x) {
+    const int h = i % cpr, row = i / cpr;  // row = plane * W + u
+    const int k = row / W, u = row - k * W;
+    cp_async<16>(stage + row * CB + 2 * h,
+                 scratch + (((size_t)lp * npl + k) * W + u) * W + c0 + 2 * h);
+  }
+  // CB consecutive counts per detector row; CB divides W/2, so the block of
+  // shifted columns does not wrap
+  const uint16_t* Ij = I + (size_t)j * W * W + (c0 + W / 2) % W;
+  if constexpr (CB >= 8) {
+    constexpr int q = CB / 8;  // 16-byte chunks per row
+    for (int i = threadIdx.x; i < W * q; i += blockDim.x) {
+      const int u = i / q, h = i - u * q;
+      cp_async<16>(cnt + u * CB + 8 * h, Ij + (size_t)((u + W / 2) % W) * W + 8 * h);
+    }
+  } else if constexpr (CB == 4) {
+    for (int u = threadIdx.x; u < W; u += blockDim.x)
+      cp_async<8>(cnt + u * 4, Ij + (size_t)((u + W / 2) % W) * W);
+  } else {
+    for (int u = threadIdx.x; u < W; u += blockDim.x)
+      cp_async<4>(cnt + u * 2, Ij + (size_t)((u + W / 2) % W) * W);
+  }
+}
+
+// GRAD = false: the modulus constraint (Eq. 7).  GRAD = true: the Fourier-
+// domain step of the amplitude-loss adjoint, G_Psi = 2 (1 - sqrt(I) / A) Psi
+// with A = sqrt(S + eps) (eps carries delta), and the loss partial sums.
+// The next patch's column block is requested while the current one is
+// transformed (double-buffered counts, one stage for the far field: it is
+// refilled once its values are in registers).  STAGE = false (the batched
+// form, one patch per call, where a prefetch has nothing to overlap) reads
+// the columns straight into registers and needs no stage.  CB is a
+// compile-time constant: with a run-time CB the per-element shared-memory
+// offsets are hoisted out of the patch loop and spill.
+template <int W, int CB, bool GRAD, bool STAGE = true>
+PTY_D void cols_body(float2* __restrict__ scratch, int M,
+       const uint16_t* __restrict__ I, const int* __restrict__ ids,
+       const float2* __restrict__ tw_g, float inv_w, float eps,
+       float* __restrict__ err_part, int npl, int xo, int ppcb, int npatch, int bx, int by) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  const int MA = M + xo;
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* stage = tw + W;                                        // MA x W x CB
+  float2* tbuf = stage + (STAGE ? MA * W * CB : 0);              // MA x CB lines
+  float* Sb = reinterpret_cast<float*>(tbuf + MA * CB * G::LP);  // M x W x CB
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(Sb + M * CB * W);  // 2 x W x CB
+  __shared__ float red[32];
+
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  const int c0 = bx * CB;
+  const int c = threadIdx.x % CB, rest = threadIdx.x / CB;
+  const int lane = rest % G::L, k = rest / G::L;
+  // k < M: the modes; k == M (with xo): the crop, forward transform only
+  const bool act = k < MA;
+  const bool mode = k < M;
+  const int kk0 = act ? k : 0;
+  float2* lbuf = tbuf + (kk0 * CB + c) * G::LP;
+  const float2* srow = stage + kk0 * W * CB + c;
+  const int nw = (blockDim.x + 31) >> 5;
+  const int p0 = by * ppcb, p1 = min(npatch, p0 + ppcb);
+  if constexpr (STAGE) {
+    if (p0 < p1) cols_stage<W, CB>(scratch, I, ids[p0], p0, npl, MA, c0, stage, cnt);
+    cp_async_commit();
+  }
+  for (int lp = p0; lp < p1; ++lp) {
+    const int j = ids[lp];
+    const uint16_t* cn = cnt + (STAGE ? ((lp - p0) & 1) * W * CB : 0);
+    float2* col = scratch + ((size_t)lp * npl + kk0) * W * W + c0 + c;
+    if constexpr (STAGE) {
+      cp_async_wait<0>();
+      __syncthreads();  // this patch's block has landed
+      if (act && lane < G::N2) {
+        float2 v[G::N1];
+#pragma unroll
+        for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = srow[(G::N2 * n1 + lane) * CB];
+        fwd_step1<W>(v, lane, tw, lbuf);
+      }
+      __syncthreads();  // the stage is free: request the next patch
+      if (lp + 1 < p1)
+        cols_stage<W, CB>(scratch, I, ids[lp + 1], lp + 1, npl, MA, c0, stage,
+                          cnt + ((lp + 1 - p0) & 1) * W * CB);
+      cp_async_commit();
+    } else {
+      // the counts and the columns are requested together: one round trip
+      float2 v[G::N1];
+      if (act && lane < G::N2) {
+#pragma unroll
+        for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = col[(size_t)(G::N2 * n1 + lane) * W];
+      }
+      {
+        const uint16_t* Ij = I + (size_t)j * W * W + (c0 + W / 2) % W;
+        for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
+          const int u = el / CB, cl = el - u * CB;
+          cnt[el] = __ldcs(Ij + (size_t)((u + W / 2) % W) * W + cl);
+        }
+      }
+      __syncthreads();  // tw (first patch); the previous patch's reads of lbuf
+      if (act && lane < G::N2) fwd_step1<W>(v, lane, tw, lbuf);
+      __syncthreads();
+    }
+    float2 z[G::N2];
+    if (act && lane < G::N1) {
+      fwd_step3<W>(z, lane, lbuf);
+      if (mode) {
+#pragma unroll
+        for (int k2 = 0; k2 < G::N2; ++k2)
+          Sb[(k * W + lane + G::N1 * k2) * CB + c] = cabs2(z[k2]);
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < G::N2; ++k2) col[(size_t)(lane + G::N1 * k2) * W] = z[k2];
+      }
+    }
+    __syncthreads();
+    // constraint factor once per detector pixel (u, c): S = sum_k |Psi_k|^2 in a
+    // fixed mode order, f = sqrt(I) / (sqrt(S) + eps) folded with both 1/W
+    // normalisations; stored over mode 0's |Psi|^2.
+    float e = 0.f;
+    {
+      const float f2 = inv_w * inv_w;
+      for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
+        const int u = el / CB, cl = el - u * CB;
+        float s = 0.f;
+        for (int kk = 0; kk < M; ++kk) s += Sb[(kk * W + u) * CB + cl];
+        const float sI = sqrtf((float)cn[el]);
+        if (!GRAD) {
+          const float a = sqrtf(s) * inv_w;
+          const float d = a - sI;
+          e = fmaf(d, d, e);
+          Sb[u * CB + cl] = sI / (a + eps) * f2;
+        } else {
+          const float a = sqrtf(fmaf(s, f2, eps));
+          const float d = a - sI;
+          e = fmaf(d, d, e);
+          Sb[u * CB + cl] = 2.f * (1.f - sI / a) * f2;
+        }
+      }
+    }
+    e = warp_sum(e);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int i = 0; i < nw; ++i) t += red[i];  // fixed order
+      err_part[(size_t)j * (W / CB) + bx] = t;
+    }
+    if (mode && lane < G::N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2)
+        z[k2] = cscale(z[k2], Sb[(lane + G::N1 * k2) * CB + c]);
+      inv_stepA<W>(z, lane, tw, lbuf);
+    }
+    __syncthreads();
+    if (mode && lane < G::N2) {
+      float2 v[G::N1];
+      inv_stepB<W>(v, lane, lbuf);
+#pragma unroll
+      for (int n1 = 0; n1 < G::N1; ++n1) col[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
+    }
+  }
+  if constexpr (STAGE) cp_async_wait<0>();
+}
+
+
+// ---------------------------------------------------------------- pass C
+// Request (cp.async) patch slot lp's far-field rows [r0, r0 + R) of the M
+// modes into `zst` ([mode][row][column]) and its crop rows into `ost`.
+template <int W>
+PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 cc, int lp,
+                          int npl, int M, int R, int r0, float2* zst, float2* ost) {
+  constexpr int hw = W / 2;  // 16-byte chunks per row
+  for (int i = threadIdx.x; i < M * R * hw; i += blockDim.x) {
+    const int line = i / hw, h = i - line * hw;  // line = mode * R + row
+    const int k = line / R, r = line - k * R;
+    cp_async<16>(zst + line * W + 2 * h,
+                 scratch + (((size_t)lp * npl + k) * W + r0 + r) * W + 2 * h);
+  }
+  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+    const int r = e / W, c = e - r * W;
+    cp_async<8>(ost + e, O + (size_t)(cc.x + r0 + r) * Hx + cc.y + c);
+  }
+}
+
+// The next patch's far-field and crop rows are requested while the current
+// patch is transformed: no registers wait on global loads.
+template <int W>
+PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
+           int R, int ppc, const int* __restrict__ ids,
+           const int2* __restrict__ corners, int npatch,
+           float2* scratch, const float* omax_part,
+           const float* pmax_part, int n_pmax,
+           const float2* __restrict__ tw_g, UpdArgs a,
+           float2* pnum, float* pden,
+           float* osum, int accumulate, int npl, int refine, int bx, int by) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  const int TB = max(M * R * G::LP, M * R * W);
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* Prow = tw + W;
+  float2* tbuf = Prow + M * R * W;  // transpose buffer, then D conj(P) terms
+  float2* num = tbuf + TB;
+  float2* ostash = num + M * R * W;  // 2 x R x W: crop rows, double-buffered
+  float2* onew = ostash + 2 * R * W; // refined crop rows (refine only)
+  float2* zst = onew + (refine ? R * W : 0);  // M x R x W far-field rows
+  float* invd = reinterpret_cast<float*>(zst + M * R * W);  // alpha_O / denominator
+  float* den = invd + R * W;
+  __shared__ float s_pmax, s_omax;
+
+  const int r0 = bx * R;
+  const int nrb = W / R;
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
+    const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
+    Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
+    num[e] = make_float2(0.f, 0.f);
+  }
+  if (threadIdx.x < 32) {
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n_pmax; i += 32) m = fmaxf(m, pmax_part[i]);
+    m = warp_max(m);
+    if (threadIdx.x == 0) s_pmax = m;
+  }
+  __syncthreads();
+  {
+    const float pmax = s_pmax;
+    const float gden = a.gamma * pmax + a.reg_eps * pmax;
+    for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+      float s = 0.f;
+      for (int k = 0; k < M; ++k) s += cabs2(Prow[k * R * W + e]);
+      const float dn = fmaf(1.f - a.gamma, s, gden);
+      invd[e] = dn > 0.f ? a.alpha_O / dn : 0.f;  // a zero denominator has a zero numerator
+      den[e] = 0.f;
+    }
+  }
+
+  const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
+  const bool act = line < M * R;
+  const int k = act ? line / R : 0, r = act ? line - k * R : 0;
+  float2* lbuf = tbuf + line * G::LP;
+  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
+  float osum_local = 0.f;
+  if (p0 < p1)
+    rows_inv_stage<W>(scratch, O, Hx, corners[ids[p0]], p0, npl, M, R, r0, zst, ostash);
+  cp_async_commit();
+  for (int lp = p0; lp < p1; ++lp) {
+    const int2 cc = corners[ids[lp]];
+    const float2* oc = ostash + ((lp - p0) & 1) * R * W;
+    if (threadIdx.x < 32) {
+      float m = 0.f;
+      for (int i = threadIdx.x; i < nrb; i += 32) m = fmaxf(m, omax_part[(size_t)lp * nrb + i]);
+      m = warp_max(m);
+      if (threadIdx.x == 0) s_omax = m;
+    }
+    cp_async_wait<0>();
+    __syncthreads();  // this patch's rows have landed
+    if (act && lane < G::N1) {
+      float2 z[G::N2];
+      const float2* src = zst + (k * R + r) * W;
+#pragma unroll
+      for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
+      inv_stepA<W>(z, lane, tw, lbuf);
+    }
+    __syncthreads();  // the far-field stage is free: request the next patch
+    if (lp + 1 < p1)
+      rows_inv_stage<W>(scratch, O, Hx, corners[ids[lp + 1]], lp + 1, npl, M, R, r0, zst,
+                        ostash + ((lp + 1 - p0) & 1) * R * W);
+    cp_async_commit();
+    float2 v[G::N1];
+    if (act && lane < G::N2) inv_stepB<W>(v, lane, lbuf);
+    __syncthreads();  // tbuf is reused below for the D conj(P) terms
+    if (act && lane < G::N2) {
+      float2* T = tbuf + (k * R + r) * W;
+      float2* nm = num + (k * R + r) * W;
+      const float2* prow = Prow + (k * R + r) * W;
+#pragma unroll
+      for (int n1 = 0; n1 < G::N1; ++n1) {
+        const int c = G::N2 * n1 + lane;
+        const float2 o = oc[r * W + c];
+        const float2 Pk = prow[c];
+        const float2 D = csub(v[n1], cmul(Pk, o));
+        T[c] = cmulc(D, Pk);
+        nm[c] = cadd(nm[c], cmulc(D, o));
+      }
+    }
+    __syncthreads();
+    const float om = s_omax;
+    for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+      const int rr = e / W, c = e - rr * W;
+      const float2 o = oc[e];
+      float2 s = make_float2(0.f, 0.f);
+      for (int kk = 0; kk < M; ++kk) s = cadd(s, tbuf[(kk * R + rr) * W + c]);
+      const float sc = invd[e];
+      const float2 onw = make_float2(fmaf(sc, s.x, o.x), fmaf(sc, s.y, o.y));
+      O[(size_t)(cc.x + r0 + rr) * Hx + cc.y + c] = onw;
+      if (refine) onew[e] = onw;
+      den[e] += fmaf(1.f - a.beta, cabs2(o), a.beta * om);
+    }
+    osum_local += om;
+    __syncthreads();
+    if (refine) {
+      // forward row DFTs of the refined crop o'_j -> plane M + 1 (XCORR_A)
+      if (line < R && lane < G::N2) {
+        float2 v2[G::N1];
+#pragma unroll
+        for (int n1 = 0; n1 < G::N1; ++n1) v2[n1] = onew[line * W + G::N2 * n1 + lane];
+        fwd_step1<W>(v2, lane, tw, tbuf + line * G::LP);
+      }
+      __syncthreads();
+      if (line < R && lane < G::N1) {
+        float2 zz[G::N2];
+        fwd_step3<W>(zz, lane, tbuf + line * G::LP);
+        float2* dst = scratch + (((size_t)lp * npl + M + 1) * W + r0 + line) * W;
+#pragma unroll
+        for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = zz[k2];
+      }
+      __syncthreads();
+    }
+  }
+  cp_async_wait<0>();
+  const int slot = by;
+  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
+    const int kk = e / (R * W), rem = e - kk * R * W, rr = rem / W, c = rem - rr * W;
+    const size_t g = (((size_t)slot * M + kk) * W + r0 + rr) * W + c;
+    pnum[g] = accumulate ? cadd(pnum[g], num[e]) : num[e];
+  }
+  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+    const int rr = e / W, c = e - rr * W;
+    const size_t g = ((size_t)slot * W + r0 + rr) * W + c;
+    pden[g] = accumulate ? pden[g] + den[e] : den[e];
+  }
+  if (bx == 0 && threadIdx.x == 0)
+    osum[slot] = accumulate ? osum[slot] + osum_local : osum_local;
+}
+
+// ------------------------------------------------------------- probe apply
+PTY_D void probe_apply_body(float2* P, int M, int WW, const float2* pnum, const float* pden,
+                            const float* osum, int nslots, float alpha_P, float reg_eps,
+                            float* pmax_part, int bx, int gx) {
+  __shared__ float red[32];
+  float os = 0.f;
+  for (int s = 0; s < nslots; ++s) os += osum[s];
+  const float guard = reg_eps * os;
+  float lmax = 0.f;
+  for (int pix = bx * blockDim.x + threadIdx.x; pix < WW; pix += gx * blockDim.x) {
+    float d = 0.f;
+    for (int s = 0; s < nslots; ++s) d += pden[(size_t)s * WW + pix];
+    const float dd = d + guard;
+    const float sc = dd > 0.f ? alpha_P / dd : 0.f;  // zero numerator too
+    float pint = 0.f;
+    for (int k = 0; k < M; ++k) {
+      float2 n = make_float2(0.f, 0.f);
+      for (int s = 0; s < nslots; ++s) n = cadd(n, pnum[((size_t)s * M + k) * WW + pix]);
+      float2 p = P[(size_t)k * WW + pix];
+      p = make_float2(fmaf(sc, n.x, p.x), fmaf(sc, n.y, p.y));
+      P[(size_t)k * WW + pix] = p;
+      pint += cabs2(p);
+    }
+    lmax = fmaxf(lmax, pint);
+  }
+  lmax = block_max(lmax, red);
+  if (threadIdx.x == 0) pmax_part[bx] = lmax;
+}
+
+// Needs blockDim.x doubles of dynamic shared memory (a static array would be
+// reserved in the persistent kernel for every task).
+PTY_D void err_reduce_body(const float* part, size_t n, double inv_sumI, float* out) {
+  extern __shared__ float4 smem4[];
+  double* red = reinterpret_cast<double*>(smem4);
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (float)(red[0] * inv_sumI);
+}
+
+}  // namespace
+
+}  // namespace pty
