@@ -59,7 +59,7 @@ def tune_problem(prob, params=None, reps=2):
     params = params or pty.rpie_params()
     Rs, ppcs, CBs, budgets, ppcbs = candidates(prob.W, prob.M)
     best = dict(prob.tiling())
-    best["scratch_bytes"] = 64 << 20
+    best["scratch_bytes"] = max(budgets)  # the largest chunk first: fewest launches
     trials = []
 
     def trial(**t):
@@ -130,7 +130,7 @@ def apply(prob, table=None):
 def _workload(W, M):
     from . import synth
     if W == 256:
-        return synth.spiral_256(n=3000)
+        return synth.spiral_256()  # the full 10^4-position scan: its group sizes
     n = 14 if W <= 96 else 10
     return synth.tiny(W=W, M=M, ny=n, nx=n, step=W / 8.0, seed=900 + W + M, photons=1e6,
                       jitter=2.0)

@@ -51,6 +51,17 @@ PTY_D float block_max(float v, float* red) {
 }
 
 // ---------------------------------------------------------------- pass A
+// Request (cp.async) the crop rows [r0, r0 + R) of patch slot lp into `ost`.
+template <int W>
+PTY_D void rows_fwd_stage(const float2* O, int Hx, int2 cc, int R, int r0, float2* ost) {
+  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+    const int r = e / W, c = e - r * W;
+    cp_async<8>(ost + e, O + (size_t)(cc.x + r0 + r) * Hx + cc.y + c);
+  }
+}
+
+// The next patch's crop rows are requested while the current patch is
+// transformed (double-buffered in shared memory).
 template <int W>
 PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
            int M, int R, int ppc, const int* __restrict__ ids,
@@ -62,52 +73,54 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* Prow = tw + W;
   float2* tbuf = Prow + M * R * W;
+  float2* ost = tbuf + (M + xo) * R * G::LP;  // 2 x R x W crop rows
   __shared__ float red[32];
 
   const int r0 = bx * R;
   const int nrb = W / R;
+  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
+  if (p0 < p1) rows_fwd_stage<W>(O, Hx, corners[ids[p0]], R, r0, ost);
+  cp_async_commit();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
     Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
   }
-  __syncthreads();
 
   // lines: (mode k, row r) for k < M, and with xo the crop itself as plane M
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
   const bool act = line < (M + xo) * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
-  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
-  // crop rows of patch lp + 1 are loaded while patch lp is transformed
-  float2 on[G::N1];
-  if (p0 < p1 && act && lane < G::N2) {
-    const int2 cc = corners[ids[p0]];
-    const float2* orow = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
-#pragma unroll
-    for (int n1 = 0; n1 < G::N1; ++n1) on[n1] = orow[G::N2 * n1 + lane];
-  }
+  const int nw = (blockDim.x + 31) >> 5;
   for (int lp = p0; lp < p1; ++lp) {
+    cp_async_wait<0>();
+    __syncthreads();  // this patch's crop rows have landed; lbuf is free
+    if (lp + 1 < p1)
+      rows_fwd_stage<W>(O, Hx, corners[ids[lp + 1]], R, r0, ost + ((lp + 1 - p0) & 1) * R * W);
+    cp_async_commit();
     float omax = 0.f;
     if (act && lane < G::N2) {
       const float2* prow = Prow + (k * R + r) * W;
+      const float2* orow = ost + ((lp - p0) & 1) * R * W + r * W;
       float2 v[G::N1];
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
-        const float2 o = on[n1];
+        const float2 o = orow[c];
         v[n1] = k < M ? cmul(prow[c], o) : o;
         omax = fmaxf(omax, cabs2(o));
       }
-      if (lp + 1 < p1) {
-        const int2 cn = corners[ids[lp + 1]];
-        const float2* orow = O + (size_t)(cn.x + r0 + r) * Hx + cn.y;
-#pragma unroll
-        for (int n1 = 0; n1 < G::N1; ++n1) on[n1] = orow[G::N2 * n1 + lane];
-      }
       fwd_step1<W>(v, lane, tw, lbuf);
     }
+    omax = warp_max(omax);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = omax;
     __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.f;
+      for (int i = 0; i < nw; ++i) m = fmaxf(m, red[i]);
+      omax_part[(size_t)lp * nrb + bx] = m;
+    }
     if (act && lane < G::N1) {
       float2 z[G::N2];
       fwd_step3<W>(z, lane, lbuf);
@@ -115,9 +128,8 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
     }
-    omax = block_max(omax, red);  // its barriers also guard lbuf reuse
-    if (threadIdx.x == 0) omax_part[(size_t)lp * nrb + bx] = omax;
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- pass B
@@ -314,7 +326,9 @@ PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 c
 }
 
 // The next patch's far-field and crop rows are requested while the current
-// patch is transformed: no registers wait on global loads.
+// patch is transformed: no registers wait on global loads.  A lane always
+// owns the same W / N2 pixels of its (mode, row) line, so its probe values
+// and its probe-numerator sums stay in registers across the patches.
 template <int W>
 PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
            int R, int ppc, const int* __restrict__ ids,
@@ -328,10 +342,8 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   extern __shared__ float4 smem4[];
   const int TB = max(M * R * G::LP, M * R * W);
   float2* tw = reinterpret_cast<float2*>(smem4);
-  float2* Prow = tw + W;
-  float2* tbuf = Prow + M * R * W;  // transpose buffer, then D conj(P) terms
-  float2* num = tbuf + TB;
-  float2* ostash = num + M * R * W;  // 2 x R x W: crop rows, double-buffered
+  float2* tbuf = tw + W;             // transpose buffer, then D conj(P) terms
+  float2* ostash = tbuf + TB;        // 2 x R x W: crop rows, double-buffered
   float2* onew = ostash + 2 * R * W; // refined crop rows (refine only)
   float2* zst = onew + (refine ? R * W : 0);  // M x R x W far-field rows
   float* invd = reinterpret_cast<float*>(zst + M * R * W);  // alpha_O / denominator
@@ -341,11 +353,6 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   const int r0 = bx * R;
   const int nrb = W / R;
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
-  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
-    const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
-    Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
-    num[e] = make_float2(0.f, 0.f);
-  }
   if (threadIdx.x < 32) {
     float m = 0.f;
     for (int i = threadIdx.x; i < n_pmax; i += 32) m = fmaxf(m, pmax_part[i]);
@@ -357,8 +364,9 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     const float pmax = s_pmax;
     const float gden = a.gamma * pmax + a.reg_eps * pmax;
     for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+      const int rr = e / W, c = e - rr * W;
       float s = 0.f;
-      for (int k = 0; k < M; ++k) s += cabs2(Prow[k * R * W + e]);
+      for (int k = 0; k < M; ++k) s += cabs2(P[((size_t)k * W + r0 + rr) * W + c]);
       const float dn = fmaf(1.f - a.gamma, s, gden);
       invd[e] = dn > 0.f ? a.alpha_O / dn : 0.f;  // a zero denominator has a zero numerator
       den[e] = 0.f;
@@ -369,6 +377,16 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   const bool act = line < M * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
+  const bool own = act && lane < G::N2;  // holds pixels c = N2 n1 + lane
+  float2 pk[G::N1], nm[G::N1];
+  {
+    const float2* prow = P + ((size_t)k * W + r0 + r) * W;
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) {
+      pk[n1] = own ? prow[G::N2 * n1 + lane] : make_float2(0.f, 0.f);
+      nm[n1] = make_float2(0.f, 0.f);
+    }
+  }
   const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
   float osum_local = 0.f;
   if (p0 < p1)
@@ -400,18 +418,15 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     float2 v[G::N1];
     if (act && lane < G::N2) inv_stepB<W>(v, lane, lbuf);
     __syncthreads();  // tbuf is reused below for the D conj(P) terms
-    if (act && lane < G::N2) {
+    if (own) {
       float2* T = tbuf + (k * R + r) * W;
-      float2* nm = num + (k * R + r) * W;
-      const float2* prow = Prow + (k * R + r) * W;
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
         const float2 o = oc[r * W + c];
-        const float2 Pk = prow[c];
-        const float2 D = csub(v[n1], cmul(Pk, o));
-        T[c] = cmulc(D, Pk);
-        nm[c] = cadd(nm[c], cmulc(D, o));
+        const float2 D = csub(v[n1], cmul(pk[n1], o));
+        T[c] = cmulc(D, pk[n1]);
+        nm[n1] = cadd(nm[n1], cmulc(D, o));
       }
     }
     __syncthreads();
@@ -450,10 +465,13 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   }
   cp_async_wait<0>();
   const int slot = by;
-  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
-    const int kk = e / (R * W), rem = e - kk * R * W, rr = rem / W, c = rem - rr * W;
-    const size_t g = (((size_t)slot * M + kk) * W + r0 + rr) * W + c;
-    pnum[g] = accumulate ? cadd(pnum[g], num[e]) : num[e];
+  if (own) {
+    float2* dst = pnum + (((size_t)slot * M + k) * W + r0 + r) * W;
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) {
+      const int c = G::N2 * n1 + lane;
+      dst[c] = accumulate ? cadd(dst[c], nm[n1]) : nm[n1];
+    }
   }
   for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
     const int rr = e / W, c = e - rr * W;

@@ -12,7 +12,7 @@ namespace pty {
 namespace {
 
 template <int W>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
            int M, int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
@@ -321,13 +321,12 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   t.thrA = round32(MA * R * L);
   t.thrC = round32(M * R * L);
   t.thrB = round32(MA * CB * L);
-  t.smA = (size_t)(W + M * R * W + MA * R * LP) * sizeof(float2);
+  t.smA = (size_t)(W + M * R * W + MA * R * LP + 2 * R * W) * sizeof(float2);
   t.smB = (size_t)(W + MA * W * CB + MA * CB * LP) * sizeof(float2) +
           (size_t)M * CB * W * sizeof(float) + (size_t)2 * W * CB * sizeof(uint16_t);
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
-  t.smC = (size_t)(W + M * R * W + TB + M * R * W + 2 * R * W + (refine ? R * W : 0) + M * R * W) *
-              sizeof(float2) +
+  t.smC = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + M * R * W) * sizeof(float2) +
           (size_t)2 * R * W * sizeof(float);
   t.n_pmax = std::max(1, std::min(1024, W * W / 256));
   return t;
