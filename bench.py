@@ -60,6 +60,14 @@ def per_pass_flops(W, M):
             "rows_inv": M * row + (24 * M + 10) * W * W}
 
 
+# DRAM bytes per pattern update of each pass, warm L2: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum with --cache-control none on
+# `bench.py --workload spiral_256_n2000` (256^2 x 5 modes, launches of ~13.5
+# patches).  Valid for the pass kernels as profiled; a launch's traffic is
+# this times its patches.
+DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.353e6, "cols": 0.399e6, "rows_inv": 0.281e6}}
+
+
 def fp32_peak_tflops():
     """148 SMs x 128 FP32 lanes x 2 flop (FMA) x 2032 MHz maximum SM clock."""
     return 148 * 128 * 2 * 2.032e9 / 1e12
@@ -315,6 +323,8 @@ def run_ours(args, wl, rank, world, local):
     flops_launch = pf.get(dom, 0.0) * wl.N / n_dom
     peak = fp32_peak_tflops()
     achieved = flops_launch / (avg_ms / 1e3) / 1e12
+    per_patch = DRAM_PER_PATCH.get((wl.W, wl.M), {}).get(dom)
+    traffic = per_patch * wl.N / n_dom if per_patch else None
     flops, bytes_ = algorithmic(wl.W, wl.M)
     hbm = measured_peaks().get("hbm_gbs", 6400.0)
 
@@ -367,7 +377,8 @@ def run_ours(args, wl, rank, world, local):
            "hbm_frac_step": value / world * bytes_ / (hbm * 1e9),
            "fp32_frac_step": value / world * flops / (peak * 1e12),
            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                        "traffic_unit": "DRAM bytes per launch (warm L2, scaled from ncu)",
                         "peak_source": "148 SM x 128 FP32 lanes x 2 x 2032 MHz",
                         "share": kst["ms"][dom] / total_ms},
            "kernel_ms": {k: kst["ms"][k] for k in kinds},
@@ -410,9 +421,39 @@ def run_batch_measure(args, dev, n_iter=5):
     ms = a.elapsed_time(e)
     n = sum(w.N for w in wls) * n_iter
     b.close()
+    # the same problems one after another, each through pty_run_iterations
+    # with its own tuned per-pass launches
+    seq_ms = run_sequential(wls, dev, n_iter, prm)
     return {"problems": 64, "iterations": n_iter, "pattern_updates": n, "ms": ms,
             "value": n / (ms / 1e3), "unit": UNIT, "launches": 1,
+            "sequential": {"ms": seq_ms, "value": n / (seq_ms / 1e3), "unit": UNIT,
+                           "what": "the 64 problems one after another, pty_run_iterations each"},
             "what": "one persistent cooperative launch (a CUDA graph) for all problems and iterations"}
+
+
+def run_sequential(wls, dev, n_iter, prm):
+    """Milliseconds for the problems run one after another (device time)."""
+    import torch
+    from paper_2205_04295_b300 import autotune, pty, synth
+    probs = []
+    for w in wls:
+        d = synth.build(w, device=dev)
+        q = pty.Problem(w.W, w.M, w.N, w.Hy, w.Hx)
+        autotune.apply(q)
+        q.set_data(synth.counts_u16(d["I"]), torch.from_numpy(d["pos"]).to(dev),
+                   torch.from_numpy(d["O0"]).to(dev), torch.from_numpy(d["P0"]).to(dev))
+        q.run(1, prm, errors=False)
+        probs.append(q)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for q in probs:
+        q.run(n_iter, prm, errors=False)
+    e.record()
+    torch.cuda.synchronize()
+    for q in probs:
+        q.close()
+    return a.elapsed_time(e)
 
 
 def main():

@@ -185,6 +185,18 @@ struct pty_handle {
   long long patches = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> event_pool;
+  // One captured plain iteration, replayed while nothing its launch
+  // arguments depend on has changed.  `epoch` counts such changes (groups
+  // rebuilt, tiling or buffers replaced, new data).
+  unsigned long long epoch = 0, iter_epoch = ~0ull;
+  cudaGraphExec_t iter_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  pty_rpie_params iter_params{};
+  double iter_inv = 0.0;
+  long long iter_launch[PTY_K_COUNT] = {0};
+  long long iter_patches = 0;
+  float* err_slot = nullptr;  // the captured iteration's error
+  bool graphs_off = false;    // capture failed once: launch directly
 
   cudaEvent_t take_event() {
     if (!event_pool.empty()) {
@@ -251,6 +263,8 @@ struct pty_handle {
     if (stream) cudaStreamSynchronize(stream);
     else cudaDeviceSynchronize();
     drain();
+    if (iter_exec) cudaGraphExecDestroy(iter_exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
     for (void* p : allocs) {
       if (ff) ff(p, stream, actx);
@@ -312,6 +326,7 @@ int regroup(pty_handle* h, int max_group) {
                      h->stream));
   h->groups_valid = true;
   h->grouped_max = max_group;
+  ++h->epoch;
   return PTY_OK;
 }
 
@@ -534,6 +549,7 @@ int pty_set_data(pty_handle* h, const uint16_t* I, const float* pos, const void*
   h->adam_t = 0;
   h->iter = 0;
   h->has_data = true;
+  ++h->epoch;
   return PTY_OK;
 }
 
@@ -550,6 +566,63 @@ int pty_set_scan_order(pty_handle* h, const int32_t* order) {
   return PTY_OK;
 }
 
+// Capture one plain iteration (every group's passes and probe update, then
+// the error reduction into err_slot) as a CUDA graph, unless the current one
+// is still valid.  Captured on a private non-blocking stream (the caller's
+// stream may be the legacy default stream, which cannot be captured) and
+// launched on the caller's stream.  If capture or instantiation fails the
+// handle falls back to direct launches of the same kernels.
+int iteration_graph(pty_handle* h, const pty_rpie_params* p, double inv) {
+  if (h->iter_exec && h->iter_epoch == h->epoch && h->iter_inv == inv &&
+      std::memcmp(&h->iter_params, p, sizeof *p) == 0)
+    return PTY_OK;
+  if (h->iter_exec) {
+    CU(cudaGraphExecDestroy(h->iter_exec));
+    h->iter_exec = nullptr;
+  }
+  if (!h->cap_stream) CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (!h->err_slot) TRY(alloc_into(h, h->err_slot, 1));
+  long long l0[PTY_K_COUNT];
+  std::memcpy(l0, h->n_launch, sizeof l0);
+  const long long p0 = h->patches;
+  cudaStream_t user = h->stream;
+  h->stream = h->cap_stream;
+  cudaGraph_t graph = nullptr;
+  int rc = PTY_OK;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const int G = (int)h->gptr.size() - 1;
+    for (int g = 0; g < G && rc == PTY_OK; ++g) rc = run_group(h, g, p);
+    if (rc == PTY_OK) {
+      pty_handle::Mark m(h, PTY_K_REDUCE);
+      e = pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_slot, h->stream);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  h->stream = user;
+  // the capture counted one iteration's launches: keep them per replay
+  for (int k = 0; k < PTY_K_COUNT; ++k) {
+    h->iter_launch[k] = h->n_launch[k] - l0[k];
+    h->n_launch[k] = l0[k];
+  }
+  h->iter_patches = h->patches - p0;
+  h->patches = p0;
+  if (e == cudaSuccess && rc == PTY_OK) e = cudaGraphInstantiate(&h->iter_exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != PTY_OK || e != cudaSuccess) {
+    cudaGetLastError();
+    h->iter_exec = nullptr;
+    h->graphs_off = true;  // direct launches from now on
+    g_err.clear();
+    return PTY_OK;
+  }
+  h->iter_epoch = h->epoch;
+  h->iter_params = *p;
+  h->iter_inv = inv;
+  return PTY_OK;
+}
+
 int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, float* err_out) {
   g_err.clear();
   TRY(check_handle(h, true));
@@ -560,6 +633,18 @@ int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, floa
   const double inv = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
   for (int it = 0; it < n_iter; ++it) {
     TRY(regroup(h, p->max_group));
+    if (!h->prof_mode && !h->graphs_off) {
+      TRY(iteration_graph(h, p, inv));
+      if (h->iter_exec) {
+        CU(cudaGraphLaunch(h->iter_exec, h->stream));
+        CU(cudaMemcpyAsync(h->err_iter + it, h->err_slot, sizeof(float),
+                           cudaMemcpyDeviceToDevice, h->stream));
+        for (int k = 0; k < PTY_K_COUNT; ++k) h->n_launch[k] += h->iter_launch[k];
+        h->patches += h->iter_patches;
+        ++h->iter;
+        continue;
+      }
+    }
     const int G = (int)h->gptr.size() - 1;
     for (int g = 0; g < G; ++g) TRY(run_group(h, g, p));
     {
@@ -960,6 +1045,7 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   h->tl = nt;
   h->Qc = Qc;
   h->err_part_n = (size_t)h->N * (W / nt.CB);
+  ++h->epoch;
   CU(pty::set_smem_limits(h->tl));
   CU(pty::set_grad_smem(h->tl));
   return PTY_OK;
