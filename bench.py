@@ -354,7 +354,7 @@ def run_ours(args, wl, rank, world, local):
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        prob.set_data(I_h, pos_h, O0_h, P0_h)
+        prob.set_data(I_h, pos_h, O0_h, P0_h, overlap=True)  # upload overlaps the passes
         prob.run(1, prm, errors=False)
         pty.check(pty.lib().pty_get_object(prob.h, O_out.data_ptr(), pty.MEM_HOST))
         pty.check(pty.lib().pty_get_probe(prob.h, P_out.data_ptr(), pty.MEM_HOST))

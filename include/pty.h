@@ -113,6 +113,20 @@ int pty_destroy(pty_handle* h);
 int pty_set_data(pty_handle* h, const uint16_t* I, const float* pos,
                  const void* O0, const void* P0, int mem_kind);
 
+/* As pty_set_data, but a host pattern stack I is not copied here: the next
+ * pty_run_iterations uploads it group by group on a second stream (one
+ * cudaMemcpyAsync per run of consecutive pattern indices, one event per
+ * group), so that group g waits only for its own patterns while the copies
+ * of later groups overlap the passes of earlier ones.  Any other call that
+ * reads the data uploads the remainder first.  The caller keeps I valid and
+ * unchanged until that upload has completed on the GPU (after the run, e.g.
+ * once a later call has synchronised the stream); page-locked I makes the
+ * copies asynchronous.  pos, O0 and P0 are copied and checked before return.
+ * With device memory it equals pty_set_data without its final synchronise.
+ * No counterpart in the paper: an input pipeline for end-to-end runs. */
+int pty_set_data_async(pty_handle* h, const uint16_t* I, const float* pos,
+                       const void* O0, const void* P0, int mem_kind);
+
 /* Optional scan order used by the greedy grouping: a permutation of 0..N-1
  * (host memory), or NULL for index order.  (The random draw, if any, is the
  * caller's.) */

@@ -192,11 +192,19 @@ struct pty_handle {
   cudaGraphExec_t iter_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
   pty_rpie_params iter_params{};
-  double iter_inv = 0.0;
   long long iter_launch[PTY_K_COUNT] = {0};
   long long iter_patches = 0;
   float* err_slot = nullptr;  // the captured iteration's error
   bool graphs_off = false;    // capture failed once: launch directly
+  // A host pattern stack whose upload pty_set_data_async deferred: the next
+  // pty_run_iterations copies it group by group on up_stream (one event per
+  // group) while the compute stream runs earlier groups.
+  const uint16_t* up_host = nullptr;
+  int up_next = 0;
+  cudaStream_t up_stream = nullptr;
+  std::vector<cudaEvent_t> up_ev;
+  cudaEvent_t up_done = nullptr;
+  bool sum_host_valid = false;  // sumI matches sum_d
 
   cudaEvent_t take_event() {
     if (!event_pool.empty()) {
@@ -265,6 +273,10 @@ struct pty_handle {
     drain();
     if (iter_exec) cudaGraphExecDestroy(iter_exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (up_stream) cudaStreamSynchronize(up_stream);
+    for (cudaEvent_t e : up_ev) cudaEventDestroy(e);
+    if (up_done) cudaEventDestroy(up_done);
+    if (up_stream) cudaStreamDestroy(up_stream);
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
     for (void* p : allocs) {
       if (ff) ff(p, stream, actx);
@@ -392,10 +404,14 @@ int ensure_err_cap(pty_handle* h, int n) {
   return PTY_OK;
 }
 
+int finish_upload(pty_handle* h);
+
+// need_data: the call reads the data, so a deferred upload is completed first.
 int check_handle(pty_handle* h, bool need_data) {
   if (!h) return fail(PTY_EINVAL, "null handle");
   if (need_data && !h->has_data) return fail(PTY_ESTATE, "pty_set_data has not been called");
   CU(cudaSetDevice(h->device));
+  if (need_data && h->up_host) TRY(finish_upload(h));
   return PTY_OK;
 }
 
@@ -406,6 +422,116 @@ int finite_check(pty_handle* h, const void* dev, size_t nfloat, const char* what
   CU(cudaMemcpyAsync(&f, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   if (f) return fail(PTY_EDATA, "%s holds a non-finite value", what);
+  return PTY_OK;
+}
+
+// Enqueue, on the upload stream, the copies of groups [up_next, g_end) of a
+// pending host pattern stack (one cudaMemcpyAsync per run of consecutive
+// pattern indices in the group) and record one event per group.
+int upload_groups(pty_handle* h, int g_end) {
+  const int G = (int)h->gptr.size() - 1;
+  g_end = std::min(g_end, G);
+  if (h->up_next >= g_end) return PTY_OK;
+  const size_t W2 = (size_t)h->W * h->W;
+  if (!h->up_stream) CU(cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking));
+  while ((int)h->up_ev.size() < G) {
+    cudaEvent_t e = nullptr;
+    CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->up_ev.push_back(e);
+  }
+  if (h->up_next == 0) {
+    // the stack is overwritten only after everything already queued on the
+    // compute stream (earlier iterations read it)
+    CU(cudaEventRecord(h->up_ev[0], h->stream));
+    CU(cudaStreamWaitEvent(h->up_stream, h->up_ev[0], 0));
+  }
+  for (; h->up_next < g_end; ++h->up_next) {
+    const int g = h->up_next;
+    for (int i = h->gptr[g], b = h->gptr[g + 1]; i < b;) {
+      const int j0 = h->gpos[i];
+      int n = 1;
+      while (i + n < b && h->gpos[i + n] == j0 + n) ++n;
+      CU(cudaMemcpyAsync(h->I + (size_t)j0 * W2, h->up_host + (size_t)j0 * W2,
+                         sizeof(uint16_t) * W2 * n, cudaMemcpyHostToDevice, h->up_stream));
+      i += n;
+    }
+    CU(cudaEventRecord(h->up_ev[g], h->up_stream));
+  }
+  return PTY_OK;
+}
+
+// Complete a pending upload: the remaining groups, then the counts sum; the
+// compute stream waits for both.
+int finish_upload(pty_handle* h) {
+  if (!h->up_host) return PTY_OK;
+  TRY(upload_groups(h, (int)h->gptr.size() - 1));
+  const size_t W2 = (size_t)h->W * h->W;
+  CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->up_stream));
+  k_sum_u16<<<296, 256, 0, h->up_stream>>>(h->I, (size_t)h->N * W2, h->sum_d);
+  CU(cudaGetLastError());
+  if (!h->up_done) CU(cudaEventCreateWithFlags(&h->up_done, cudaEventDisableTiming));
+  CU(cudaEventRecord(h->up_done, h->up_stream));
+  CU(cudaStreamWaitEvent(h->stream, h->up_done, 0));
+  h->up_host = nullptr;
+  return PTY_OK;
+}
+
+// The host copy of sum(I), fetched once after a deferred or device upload.
+int host_sum(pty_handle* h) {
+  TRY(finish_upload(h));
+  if (h->sum_host_valid) return PTY_OK;
+  unsigned long long s = 0;
+  CU(cudaMemcpyAsync(&s, h->sum_d, sizeof s, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->sumI = (double)s;
+  h->sum_host_valid = true;
+  return PTY_OK;
+}
+
+// pty_set_data and pty_set_data_async.  With defer and host memory the
+// pattern stack is left pending: the next pty_run_iterations uploads it
+// group by group (any other call that needs it uploads it whole first).
+int set_data_impl(pty_handle* h, const uint16_t* I, const float* pos, const void* O0,
+                  const void* P0, int mem_kind, bool defer) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  TRY(check_mem_kind(mem_kind));
+  if (!I || !pos || !O0 || !P0) return fail(PTY_EINVAL, "null data pointer");
+  const size_t W2 = (size_t)h->W * h->W;
+  h->has_data = false;
+  h->up_host = nullptr;  // a pending upload is superseded
+  h->pos_h.resize(2 * (size_t)h->N);
+  CU(cudaMemcpyAsync(h->pos_h.data(), pos, sizeof(float) * 2 * h->N,
+                     mem_kind == PTY_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->groups_valid = false;
+  TRY(regroup(h, 0));
+  CU(cudaMemcpyAsync(h->pos, h->pos_h.data(), sizeof(float) * 2 * h->N, cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaMemcpyAsync(h->O, O0, sizeof(float2) * h->Hy * h->Hx, kind_in(mem_kind), h->stream));
+  CU(cudaMemcpyAsync(h->P, P0, sizeof(float2) * h->M * W2, kind_in(mem_kind), h->stream));
+  TRY(finite_check(h, h->O, (size_t)2 * h->Hy * h->Hx, "object"));
+  TRY(finite_check(h, h->P, (size_t)2 * h->M * W2, "probe"));
+  CU(cudaMemsetAsync(h->am, 0, sizeof(float) * 2 * h->N, h->stream));
+  CU(cudaMemsetAsync(h->av, 0, sizeof(float) * 2 * h->N, h->stream));
+  CU(cudaMemsetAsync(h->shift, 0, sizeof(float) * 2 * h->N, h->stream));
+  CU(pty::launch_pmax(h->tl, h->P, h->pmax_part, h->stream));
+  h->sum_host_valid = false;
+  if (defer && mem_kind == PTY_MEM_HOST) {
+    h->up_host = I;
+    h->up_next = 0;
+  } else {
+    CU(cudaMemcpyAsync(h->I, I, sizeof(uint16_t) * h->N * W2, kind_in(mem_kind), h->stream));
+    CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->stream));
+    k_sum_u16<<<296, 256, 0, h->stream>>>(h->I, (size_t)h->N * W2, h->sum_d);
+    CU(cudaGetLastError());
+    if (!defer) TRY(host_sum(h));  // synchronises: the caller may reuse its buffers
+  }
+  h->adam_t = 0;
+  h->iter = 0;
+  h->has_data = true;
+  ++h->epoch;
   return PTY_OK;
 }
 
@@ -515,42 +641,12 @@ int pty_destroy(pty_handle* h) {
 
 int pty_set_data(pty_handle* h, const uint16_t* I, const float* pos, const void* O0,
                  const void* P0, int mem_kind) {
-  g_err.clear();
-  TRY(check_handle(h, false));
-  TRY(check_mem_kind(mem_kind));
-  if (!I || !pos || !O0 || !P0) return fail(PTY_EINVAL, "null data pointer");
-  const size_t W2 = (size_t)h->W * h->W;
-  h->has_data = false;
-  h->pos_h.resize(2 * (size_t)h->N);
-  CU(cudaMemcpyAsync(h->pos_h.data(), pos, sizeof(float) * 2 * h->N,
-                     mem_kind == PTY_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost,
-                     h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  h->groups_valid = false;
-  TRY(regroup(h, 0));
-  CU(cudaMemcpyAsync(h->I, I, sizeof(uint16_t) * h->N * W2, kind_in(mem_kind), h->stream));
-  CU(cudaMemcpyAsync(h->pos, h->pos_h.data(), sizeof(float) * 2 * h->N, cudaMemcpyHostToDevice,
-                     h->stream));
-  CU(cudaMemcpyAsync(h->O, O0, sizeof(float2) * h->Hy * h->Hx, kind_in(mem_kind), h->stream));
-  CU(cudaMemcpyAsync(h->P, P0, sizeof(float2) * h->M * W2, kind_in(mem_kind), h->stream));
-  TRY(finite_check(h, h->O, (size_t)2 * h->Hy * h->Hx, "object"));
-  TRY(finite_check(h, h->P, (size_t)2 * h->M * W2, "probe"));
-  CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->stream));
-  k_sum_u16<<<296, 256, 0, h->stream>>>(h->I, (size_t)h->N * W2, h->sum_d);
-  CU(cudaGetLastError());
-  unsigned long long s = 0;
-  CU(cudaMemcpyAsync(&s, h->sum_d, sizeof s, cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaMemsetAsync(h->am, 0, sizeof(float) * 2 * h->N, h->stream));
-  CU(cudaMemsetAsync(h->av, 0, sizeof(float) * 2 * h->N, h->stream));
-  CU(cudaMemsetAsync(h->shift, 0, sizeof(float) * 2 * h->N, h->stream));
-  CU(pty::launch_pmax(h->tl, h->P, h->pmax_part, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  h->sumI = (double)s;
-  h->adam_t = 0;
-  h->iter = 0;
-  h->has_data = true;
-  ++h->epoch;
-  return PTY_OK;
+  return set_data_impl(h, I, pos, O0, P0, mem_kind, false);
+}
+
+int pty_set_data_async(pty_handle* h, const uint16_t* I, const float* pos, const void* O0,
+                       const void* P0, int mem_kind) {
+  return set_data_impl(h, I, pos, O0, P0, mem_kind, true);
 }
 
 int pty_set_scan_order(pty_handle* h, const int32_t* order) {
@@ -572,8 +668,8 @@ int pty_set_scan_order(pty_handle* h, const int32_t* order) {
 // stream may be the legacy default stream, which cannot be captured) and
 // launched on the caller's stream.  If capture or instantiation fails the
 // handle falls back to direct launches of the same kernels.
-int iteration_graph(pty_handle* h, const pty_rpie_params* p, double inv) {
-  if (h->iter_exec && h->iter_epoch == h->epoch && h->iter_inv == inv &&
+int iteration_graph(pty_handle* h, const pty_rpie_params* p) {
+  if (h->iter_exec && h->iter_epoch == h->epoch &&
       std::memcmp(&h->iter_params, p, sizeof *p) == 0)
     return PTY_OK;
   if (h->iter_exec) {
@@ -595,7 +691,7 @@ int iteration_graph(pty_handle* h, const pty_rpie_params* p, double inv) {
     for (int g = 0; g < G && rc == PTY_OK; ++g) rc = run_group(h, g, p);
     if (rc == PTY_OK) {
       pty_handle::Mark m(h, PTY_K_REDUCE);
-      e = pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_slot, h->stream);
+      e = pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_slot, h->stream);
     }
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
     if (e == cudaSuccess) e = e2;
@@ -619,22 +715,39 @@ int iteration_graph(pty_handle* h, const pty_rpie_params* p, double inv) {
   }
   h->iter_epoch = h->epoch;
   h->iter_params = *p;
-  h->iter_inv = inv;
   return PTY_OK;
 }
 
 int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, float* err_out) {
   g_err.clear();
-  TRY(check_handle(h, true));
+  TRY(check_handle(h, false));
+  if (!h->has_data) return fail(PTY_ESTATE, "pty_set_data has not been called");
   TRY(check_params(p));
   if (n_iter < 0) return fail(PTY_EINVAL, "n_iter < 0");
-  if (n_iter == 0) return PTY_OK;
+  if (n_iter == 0) return finish_upload(h);
   TRY(ensure_err_cap(h, n_iter));
-  const double inv = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
   for (int it = 0; it < n_iter; ++it) {
     TRY(regroup(h, p->max_group));
+    if (h->up_host) {
+      // first iteration after pty_set_data_async: group g waits only for its
+      // own patterns, which were queued two groups ahead
+      const int G = (int)h->gptr.size() - 1;
+      for (int g = 0; g < G; ++g) {
+        TRY(upload_groups(h, g + 3));
+        CU(cudaStreamWaitEvent(h->stream, h->up_ev[g], 0));
+        TRY(run_group(h, g, p));
+      }
+      TRY(finish_upload(h));  // the counts sum for the error
+      {
+        pty_handle::Mark m(h, PTY_K_REDUCE);
+        CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter + it,
+                                  h->stream));
+      }
+      ++h->iter;
+      continue;
+    }
     if (!h->prof_mode && !h->graphs_off) {
-      TRY(iteration_graph(h, p, inv));
+      TRY(iteration_graph(h, p));
       if (h->iter_exec) {
         CU(cudaGraphLaunch(h->iter_exec, h->stream));
         CU(cudaMemcpyAsync(h->err_iter + it, h->err_slot, sizeof(float),
@@ -649,7 +762,7 @@ int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, floa
     for (int g = 0; g < G; ++g) TRY(run_group(h, g, p));
     {
       pty_handle::Mark m(h, PTY_K_REDUCE);
-      CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter + it, h->stream));
+      CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter + it, h->stream));
     }
     ++h->iter;
   }
@@ -695,7 +808,6 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
   }
   if (n_iter == 0) return PTY_OK;
   TRY(ensure_err_cap(h, n_iter));
-  const double inv = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
   for (int it = 0; it < n_iter; ++it) {
     TRY(regroup(h, p->max_group));
     const bool on = h->iter >= r->start_iter;
@@ -706,7 +818,7 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
       // the partial sums of this iteration follow its column-pass tiling
       const size_t nerr = (size_t)h->N * (h->W / (on ? h->tlr.CB : h->tl.CB));
       pty_handle::Mark m(h, PTY_K_REDUCE);
-      CU(pty::launch_err_reduce(h->err_part, nerr, inv, h->err_iter + it, h->stream));
+      CU(pty::launch_err_reduce(h->err_part, nerr, 0.0, h->sum_d, h->err_iter + it, h->stream));
     }
     if (on) {
       ++h->adam_t;
@@ -846,8 +958,7 @@ int pty_run_groups(pty_handle* h, int g_begin, int g_end, const pty_rpie_params*
   CU(cudaMemsetAsync(h->err_part, 0, sizeof(float) * h->err_part_n, h->stream));
   for (int g = g_begin; g < g_end; ++g) TRY(run_group(h, g, p));
   if (err_out) {
-    const double inv = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
-    CU(pty::launch_err_reduce(h->err_part, h->err_part_n, inv, h->err_iter, h->stream));
+    CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter, h->stream));
     CU(cudaMemcpyAsync(err_out, h->err_iter, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
   }
@@ -1230,6 +1341,7 @@ int pty_batch_run(pty_batch* b, int n_iter, const pty_rpie_params* p) {
     pb.W = h->W; pb.M = h->M; pb.N = h->N; pb.Hx = h->Hx;
     pb.R = t.R; pb.ppc = t.ppc; pb.CB = t.CB; pb.n_pmax = t.n_pmax;
     pb.inv_w = h->inv_w; pb.update_probe = p->update_probe; pb.a = upd_args(p);
+    TRY(host_sum(h));
     pb.inv_sumI = h->sumI > 0 ? 1.0 / h->sumI : 0.0;
     pb.tw = h->tw; pb.O = h->O; pb.P = h->P; pb.I = h->I; pb.corners = h->corners;
     pb.gpos = h->gpos_d; pb.scratch = h->scratch; pb.pnum = h->pnum; pb.pden = h->pden;

@@ -85,7 +85,7 @@ __device__ __forceinline__ void batch_task(const BatchProb& pb, const BatchTask&
       }
       break;
     default:
-      err_reduce_body(pb.err_part, pb.err_part_n, pb.inv_sumI, pb.err_iter + tk.it);
+      err_reduce_body(pb.err_part, pb.err_part_n, pb.inv_sumI, nullptr, pb.err_iter + tk.it);
       break;
   }
 }

@@ -92,8 +92,9 @@ cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
                                cudaStream_t s);
 cudaError_t launch_pmax(const Tiling& t, const float2* P, float* pmax_part,
                         cudaStream_t s);
+// Error normalised by 1/sum(I): inv_sumI, or the device sum when sum_dev != NULL.
 cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
-                              float* out, cudaStream_t s);
+                              const unsigned long long* sum_dev, float* out, cudaStream_t s);
 cudaError_t launch_cols_intensity(const Tiling& t, const float2* scratch,
                                   const int* ids, int npatch, const float2* tw,
                                   float inv_w, float* out, cudaStream_t s);

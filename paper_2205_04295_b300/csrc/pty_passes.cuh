@@ -513,7 +513,10 @@ PTY_D void probe_apply_body(float2* P, int M, int WW, const float2* pnum, const 
 
 // Needs blockDim.x doubles of dynamic shared memory (a static array would be
 // reserved in the persistent kernel for every task).
-PTY_D void err_reduce_body(const float* part, size_t n, double inv_sumI, float* out) {
+// The normalisation is 1 / sum(I): inv_sumI, or, when sum_dev is given, the
+// device-resident counts sum (so that no host value waits for an upload).
+PTY_D void err_reduce_body(const float* part, size_t n, double inv_sumI,
+                           const unsigned long long* sum_dev, float* out) {
   extern __shared__ float4 smem4[];
   double* red = reinterpret_cast<double*>(smem4);
   double s = 0.0;
@@ -524,7 +527,11 @@ PTY_D void err_reduce_body(const float* part, size_t n, double inv_sumI, float* 
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = (float)(red[0] * inv_sumI);
+  if (threadIdx.x == 0) {
+    double inv = inv_sumI;
+    if (sum_dev) inv = *sum_dev ? 1.0 / (double)*sum_dev : 0.0;
+    *out = (float)(red[0] * inv);
+  }
 }
 
 }  // namespace

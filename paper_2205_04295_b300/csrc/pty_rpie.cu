@@ -66,8 +66,9 @@ k_pmax(const float2* __restrict__ P, int M, int WW, float* __restrict__ pmax_par
 }
 
 __global__ void __launch_bounds__(1024)
-k_err_reduce(const float* __restrict__ part, size_t n, double inv_sumI, float* out) {
-  err_reduce_body(part, n, inv_sumI, out);
+k_err_reduce(const float* __restrict__ part, size_t n, double inv_sumI,
+             const unsigned long long* sum_dev, float* out) {
+  err_reduce_body(part, n, inv_sumI, sum_dev, out);
 }
 
 // Model intensities: forward column DFTs after pass A, S written out.
@@ -435,9 +436,9 @@ cudaError_t launch_pmax(const Tiling& t, const float2* P, float* pmax_part, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI, float* out,
-                              cudaStream_t s) {
-  k_err_reduce<<<1, 1024, 1024 * sizeof(double), s>>>(err_part, n, inv_sumI, out);
+cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
+                              const unsigned long long* sum_dev, float* out, cudaStream_t s) {
+  k_err_reduce<<<1, 1024, 1024 * sizeof(double), s>>>(err_part, n, inv_sumI, sum_dev, out);
   return cudaGetLastError();
 }
 

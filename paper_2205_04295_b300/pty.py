@@ -84,6 +84,7 @@ _SIGS = {
     "pty_init_problem": (c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(c_void_p)]),
     "pty_destroy": (c_int, [c_void_p]),
     "pty_set_data": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "pty_set_data_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "pty_set_scan_order": (c_int, [c_void_p, c_void_p]),
     "pty_run_iterations": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams), c_void_p]),
     "pty_refine_positions": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams),
@@ -219,8 +220,9 @@ class Problem:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().pty_destroy(self.h)
+            lib().pty_destroy(self.h)  # synchronises: a pending stack is no longer read
             self.h = None
+        self._pending_stack = None
 
     def __del__(self):
         try:
@@ -235,14 +237,21 @@ class Problem:
         self.close()
 
     # -- data
-    def set_data(self, I, pos, O0, P0):
+    def set_data(self, I, pos, O0, P0, overlap=False):
+        """Copy in the data.  overlap=True (pty_set_data_async): a host pattern
+        stack is uploaded during the next run(), group by group, while earlier
+        groups compute; pinned host memory makes the copies asynchronous.
+        The stack is kept referenced here until the next set_data or close,
+        and must not be modified before the run has finished on the GPU."""
         pI, k1, a1 = _ptr(I, _dt("u16"))
         pp, k2, a2 = _ptr(pos, _dt("f32"))
         pO, k3, a3 = _ptr(O0, _dt("c64"))
         pP, k4, a4 = _ptr(P0, _dt("c64"))
         if len({k1, k2, k3, k4}) != 1:
             raise ValueError("all of I, pos, O0, P0 must live in the same memory (host or device)")
-        check(lib().pty_set_data(self.h, pI, pp, pO, pP, k1))
+        fn = lib().pty_set_data_async if overlap else lib().pty_set_data
+        check(fn(self.h, pI, pp, pO, pP, k1))
+        self._pending_stack = a1 if overlap else None
 
     def set_scan_order(self, order):
         if order is None:

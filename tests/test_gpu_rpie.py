@@ -143,6 +143,40 @@ def test_graph_replay_equals_direct_launches():
     assert runs[0][4] == runs[1][4] == 9 * wl.N
 
 
+def test_deferred_upload_equals_set_data():
+    """pty_set_data_async uploads the stack group by group inside the next
+    run (or whole, before any other call that reads it): the results must be
+    bitwise those of pty_set_data, for pinned and pageable host stacks."""
+    import torch
+    wl = synth.tiny(W=64, M=2, ny=6, nx=6, step=10.0, seed=72)
+    d = build(wl)
+    ref = gpu_problem(wl, d)
+    dev = torch.device("cuda")
+    Ot, Pt = torch.from_numpy(d["O0"]).to(dev), torch.from_numpy(d["P0"]).to(dev)
+    post = torch.from_numpy(d["pos"]).to(dev)
+    L_ref = float(ref.loss(Ot, Pt, post))
+    e_ref = ref.run(2)
+    O_ref, P_ref = ref.object(False), ref.probe(False)
+    for pinned in (True, False):
+        I = torch.from_numpy(d["I"].astype(np.int32)).to(torch.uint16)
+        if pinned:
+            I = I.pin_memory()
+        from paper_2205_04295_b300 import pty
+        prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
+        prob.set_data(I, torch.from_numpy(d["pos"]), torch.from_numpy(d["O0"]),
+                      torch.from_numpy(d["P0"]), overlap=True)
+        e = prob.run(2)
+        np.testing.assert_array_equal(e, e_ref)
+        np.testing.assert_array_equal(prob.object(False), O_ref)
+        np.testing.assert_array_equal(prob.probe(False), P_ref)
+        # a call that reads the counts before any run uploads the stack whole
+        prob.set_data(I, torch.from_numpy(d["pos"]), torch.from_numpy(d["O0"]),
+                      torch.from_numpy(d["P0"]), overlap=True)
+        assert float(prob.loss(Ot, Pt, post)) == L_ref
+        np.testing.assert_array_equal(prob.run(2), e_ref)
+        prob.close()
+
+
 def test_edge_cases_single_position_corner_and_dark_pattern():
     wl = synth.tiny(W=32, M=1, ny=1, nx=1, step=1.0, seed=15)
     d = build(wl)
