@@ -310,6 +310,7 @@ def run_ours(args, wl, rank, world, local):
     del unf
 
     # ---- per-kernel durations, CUDA events on the library's stream
+    prob.stats(reset=True)  # counts of this one iteration only
     prob.profile(1)
     prob.run(1, prm, errors=False)
     kst = prob.stats(reset=True)

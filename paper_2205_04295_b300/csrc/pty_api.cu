@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -58,6 +59,30 @@ __global__ void k_sum_u16(const uint16_t* __restrict__ I, size_t n,
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);  // integer: exact in any order
 }
 
+// Copy patterns ids[0..n) (W2 counts each, W2 a multiple of 8) from host
+// memory the device can address (page-locked, unified addressing) into the
+// device stack, and add their counts to *sum (integers: exact in any order).
+// Reads cross the host link; one launch moves a whole group.
+__global__ void k_gather_host(uint16_t* __restrict__ dst, const uint16_t* __restrict__ src,
+                              const int* __restrict__ ids, int n, int W2,
+                              unsigned long long* sum) {
+  const int per = W2 / 8;  // 16-byte vectors per pattern
+  const long long total = (long long)n * per;
+  unsigned long long s = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i / per), e = (int)(i - (long long)p * per);
+    const size_t off = (size_t)ids[p] * W2;
+    const uint4 v = reinterpret_cast<const uint4*>(src + off)[e];
+    reinterpret_cast<uint4*>(dst + off)[e] = v;
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += (w[q] & 0xffffu) + (w[q] >> 16);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(sum, s);
+}
+
 __global__ void k_iota(int* p, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     p[i] = i;
@@ -66,6 +91,11 @@ __global__ void k_iota(int* p, int n) {
 // Greedy first-fit grouping.  Boxes with corners a, b overlap iff
 // |a.y - b.y| < W and |a.x - b.x| < W; only the 3x3 neighbouring cells of a
 // W-sized grid can hold an overlapping corner.
+// First-fit grouping in scan order into groups of pairwise-disjoint W x W
+// boxes.  Two corners in the same W x W cell of a grid always overlap, so a
+// group holds at most one member per cell: each group keeps a cell table and
+// a position tests at most the 3 x 3 cells around its own in each group it
+// tries.
 void greedy_group(const std::vector<int2>& c, int W, const int32_t* order,
                   int max_group, std::vector<int>& gptr, std::vector<int>& gpos) {
   const int N = (int)c.size();
@@ -77,32 +107,39 @@ void greedy_group(const std::vector<int2>& c, int W, const int32_t* order,
     if (j == 0 || c[j].y > maxx) maxx = c[j].y;
   }
   const int ncy = (maxy - miny) / W + 1, ncx = (maxx - minx) / W + 1;
-  std::vector<std::vector<int>> cells((size_t)ncy * ncx);
-  std::vector<int> group_of(N, -1), gsize, stamp;
+  const size_t ncell = (size_t)ncy * ncx;
+  std::vector<int> table;  // [group][cell] -> member index or -1
+  std::vector<int> gsize;
   std::vector<std::vector<int>> members;
   for (int n = 0; n < N; ++n) {
     const int j = order ? order[n] : n;
     const int cy = (c[j].x - miny) / W, cx = (c[j].y - minx) / W;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int yy = cy + dy, xx = cx + dx;
-        if (yy < 0 || xx < 0 || yy >= ncy || xx >= ncx) continue;
-        for (int i : cells[(size_t)yy * ncx + xx])
-          if (std::abs(c[i].x - c[j].x) < W && std::abs(c[i].y - c[j].y) < W)
-            stamp[group_of[i]] = n;
-      }
-    int g = 0;
     const int G = (int)members.size();
-    while (g < G && (stamp[g] == n || (max_group > 0 && gsize[g] >= max_group))) ++g;
+    int g = 0;
+    for (; g < G; ++g) {
+      if (max_group > 0 && gsize[g] >= max_group) continue;
+      const int* tg = table.data() + (size_t)g * ncell;
+      bool clash = false;
+      for (int dy = -1; dy <= 1 && !clash; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int yy = cy + dy, xx = cx + dx;
+          if (yy < 0 || xx < 0 || yy >= ncy || xx >= ncx) continue;
+          const int i = tg[(size_t)yy * ncx + xx];
+          if (i >= 0 && std::abs(c[i].x - c[j].x) < W && std::abs(c[i].y - c[j].y) < W) {
+            clash = true;
+            break;
+          }
+        }
+      if (!clash) break;
+    }
     if (g == G) {
       members.emplace_back();
       gsize.push_back(0);
-      stamp.push_back(-1);
+      table.resize(table.size() + ncell, -1);
     }
     members[g].push_back(j);
     ++gsize[g];
-    group_of[j] = g;
-    cells[(size_t)cy * ncx + cx].push_back(j);
+    table[(size_t)g * ncell + (size_t)cy * ncx + cx] = j;
   }
   gptr.assign(members.size() + 1, 0);
   gpos.clear();
@@ -177,6 +214,8 @@ struct pty_handle {
   std::vector<int32_t> order;
   bool groups_valid = false;
   int grouped_max = -1;
+  std::vector<int2> grouped_corners;  // inputs of the current groups
+  std::vector<int32_t> grouped_order;
   std::vector<void*> allocs;
   // accounting
   int prof_mode = 0;
@@ -200,6 +239,7 @@ struct pty_handle {
   // pty_run_iterations copies it group by group on up_stream (one event per
   // group) while the compute stream runs earlier groups.
   const uint16_t* up_host = nullptr;
+  const uint16_t* up_dev = nullptr;  // up_host as the device addresses it, if it can
   int up_next = 0;
   cudaStream_t up_stream = nullptr;
   std::vector<cudaEvent_t> up_ev;
@@ -330,8 +370,19 @@ int regroup(pty_handle* h, int max_group) {
                   j, cy, cx, h->Hy, h->Hx);
     h->corners_h[j] = make_int2(cy, cx);
   }
+  // the grouping is a function of the corners, the scan order and max_group
+  // only: unchanged inputs (same scan with new data, registration steps that
+  // move no corner) keep the groups already on the device
+  if (h->grouped_max == max_group && !h->gptr.empty() && h->grouped_order == h->order &&
+      h->grouped_corners.size() == (size_t)N &&
+      std::memcmp(h->grouped_corners.data(), h->corners_h.data(), sizeof(int2) * N) == 0) {
+    h->groups_valid = true;
+    return PTY_OK;
+  }
   greedy_group(h->corners_h, W, h->order.empty() ? nullptr : h->order.data(), max_group,
                h->gptr, h->gpos);
+  h->grouped_corners = h->corners_h;
+  h->grouped_order = h->order;
   CU(cudaMemcpyAsync(h->corners, h->corners_h.data(), sizeof(int2) * N,
                      cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemcpyAsync(h->gpos_d, h->gpos.data(), sizeof(int) * N, cudaMemcpyHostToDevice,
@@ -433,7 +484,12 @@ int upload_groups(pty_handle* h, int g_end) {
   g_end = std::min(g_end, G);
   if (h->up_next >= g_end) return PTY_OK;
   const size_t W2 = (size_t)h->W * h->W;
-  if (!h->up_stream) CU(cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking));
+  if (!h->up_stream) {
+    // highest priority: its small gather kernels take SM slots ahead of the passes
+    int lo = 0, hi = 0;
+    CU(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CU(cudaStreamCreateWithPriority(&h->up_stream, cudaStreamNonBlocking, hi));
+  }
   while ((int)h->up_ev.size() < G) {
     cudaEvent_t e = nullptr;
     CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -444,9 +500,19 @@ int upload_groups(pty_handle* h, int g_end) {
     // compute stream (earlier iterations read it)
     CU(cudaEventRecord(h->up_ev[0], h->stream));
     CU(cudaStreamWaitEvent(h->up_stream, h->up_ev[0], 0));
+    if (h->up_dev) CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->up_stream));
   }
   for (; h->up_next < g_end; ++h->up_next) {
     const int g = h->up_next;
+    if (h->up_dev) {
+      // one gather kernel per group, summing the counts on the way
+      k_gather_host<<<64, 256, 0, h->up_stream>>>(h->I, h->up_dev, h->gpos_d + h->gptr[g],
+                                                   h->gptr[g + 1] - h->gptr[g], (int)W2,
+                                                   h->sum_d);
+      CU(cudaGetLastError());
+      CU(cudaEventRecord(h->up_ev[g], h->up_stream));
+      continue;
+    }
     for (int i = h->gptr[g], b = h->gptr[g + 1]; i < b;) {
       const int j0 = h->gpos[i];
       int n = 1;
@@ -465,10 +531,12 @@ int upload_groups(pty_handle* h, int g_end) {
 int finish_upload(pty_handle* h) {
   if (!h->up_host) return PTY_OK;
   TRY(upload_groups(h, (int)h->gptr.size() - 1));
-  const size_t W2 = (size_t)h->W * h->W;
-  CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->up_stream));
-  k_sum_u16<<<296, 256, 0, h->up_stream>>>(h->I, (size_t)h->N * W2, h->sum_d);
-  CU(cudaGetLastError());
+  if (!h->up_dev) {  // the gather kernels summed the counts already
+    const size_t W2 = (size_t)h->W * h->W;
+    CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->up_stream));
+    k_sum_u16<<<296, 256, 0, h->up_stream>>>(h->I, (size_t)h->N * W2, h->sum_d);
+    CU(cudaGetLastError());
+  }
   if (!h->up_done) CU(cudaEventCreateWithFlags(&h->up_done, cudaEventDisableTiming));
   CU(cudaEventRecord(h->up_done, h->up_stream));
   CU(cudaStreamWaitEvent(h->stream, h->up_done, 0));
@@ -520,7 +588,16 @@ int set_data_impl(pty_handle* h, const uint16_t* I, const float* pos, const void
   h->sum_host_valid = false;
   if (defer && mem_kind == PTY_MEM_HOST) {
     h->up_host = I;
+    h->up_dev = nullptr;
     h->up_next = 0;
+    // page-locked host memory the device can address is gathered by kernels;
+    // anything else goes through cudaMemcpyAsync
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, I) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer && reinterpret_cast<uintptr_t>(pa.devicePointer) % 16 == 0 &&
+        W2 % 8 == 0)
+      h->up_dev = static_cast<const uint16_t*>(pa.devicePointer);
+    cudaGetLastError();
   } else {
     CU(cudaMemcpyAsync(h->I, I, sizeof(uint16_t) * h->N * W2, kind_in(mem_kind), h->stream));
     CU(cudaMemsetAsync(h->sum_d, 0, sizeof(unsigned long long), h->stream));
