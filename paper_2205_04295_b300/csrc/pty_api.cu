@@ -1201,14 +1201,22 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   if (t->ppcb > 0) nt.ppcb = t->ppcb;
   if (nt.smA > 227 * 1024 || nt.smB > 227 * 1024 || nt.smC > 227 * 1024)
     return fail(PTY_EINVAL, "tiling needs too much shared memory");
+  // the registration passes take the same geometry where it fits their extra
+  // crop plane, and the same patches per chunk
+  pty::Tiling nr = pty::make_tiling(W, M, true, 512, t->R, t->ppc, t->CB);
+  if (t->ppcb > 0) nr.ppcb = t->ppcb;
+  if ((t->R && (M + 1) * t->R * L > 256) || (t->CB && (M + 1) * t->CB * L > 384) ||
+      nr.smA > 227 * 1024 || nr.smB > 227 * 1024 || nr.smC > 227 * 1024)
+    nr = h->tlr;
   const size_t W2 = (size_t)W * W;
   const size_t budget = t->scratch_bytes ? t->scratch_bytes : ((size_t)64 << 20);
   const int Qc = (int)std::min<size_t>((size_t)h->N, std::max<size_t>(1, budget / (W2 * M * sizeof(float2))));
+  const int Qcr = Qc;
   // grow the buffers whose size depends on the tiling
   // slots for this ppc and for the default ppc (4) the batched form uses
-  const int ppc_min = std::min(nt.ppc, 4);
-  const int nslots = (std::max(std::max(Qc, h->Qcr), h->Qcg) + ppc_min - 1) / ppc_min;
-  const size_t scratch = std::max(std::max((size_t)Qc * M, (size_t)h->Qcr * h->tlr.npl),
+  const int ppc_min = std::min(std::min(nt.ppc, nr.ppc), 4);
+  const int nslots = (std::max(std::max(Qc, Qcr), h->Qcg) + ppc_min - 1) / ppc_min;
+  const size_t scratch = std::max(std::max((size_t)Qc * M, (size_t)Qcr * nr.npl),
                                   (size_t)h->Qcg * (M + 1)) * W2;
   const size_t cur_scratch = std::max(std::max((size_t)h->Qc * M, (size_t)h->Qcr * h->tlr.npl),
                                       (size_t)h->Qcg * (M + 1)) * W2;
@@ -1218,6 +1226,17 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
     h->scratch = nullptr;
     TRY(alloc_into(h, h->scratch, scratch));
   }
+  if (Qcr > h->Qcr) {
+    h->dfree(h->cval); h->dfree(h->cidx);
+    h->cval = nullptr; h->cidx = nullptr;
+    TRY(alloc_into(h, h->cval, (size_t)Qcr * W));
+    TRY(alloc_into(h, h->cidx, (size_t)Qcr * W));
+    if (h->upart) {
+      h->dfree(h->upart);
+      h->upart = nullptr;
+      TRY(alloc_into(h, h->upart, (size_t)Qcr * (W / 16) * h->rg.K * h->rg.K));
+    }
+  }
   if (nslots > h->nslots) {
     h->dfree(h->pnum); h->dfree(h->pden); h->dfree(h->osum);
     h->pnum = nullptr; h->pden = nullptr; h->osum = nullptr;
@@ -1226,15 +1245,18 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
     TRY(alloc_into(h, h->osum, (size_t)nslots));
     h->nslots = nslots;
   }
-  const size_t omax_need = (size_t)std::max(Qc, h->Qcr) * (W / std::min(nt.R, h->tlr.R));
+  const size_t omax_need = (size_t)std::max(Qc, Qcr) * (W / std::min(nt.R, nr.R));
   h->dfree(h->omax_part);
   h->omax_part = nullptr;
-  TRY(alloc_into(h, h->omax_part, std::max(omax_need, (size_t)std::max(h->Qc, h->Qcr) * W)));
+  TRY(alloc_into(h, h->omax_part, std::max(omax_need, (size_t)std::max(Qc, Qcr) * W)));
   h->tl = nt;
+  h->tlr = nr;
   h->Qc = Qc;
+  h->Qcr = Qcr;
   h->err_part_n = (size_t)h->N * (W / nt.CB);
   ++h->epoch;
   CU(pty::set_smem_limits(h->tl));
+  CU(pty::set_smem_limits(h->tlr));
   CU(pty::set_grad_smem(h->tl));
   return PTY_OK;
 }
