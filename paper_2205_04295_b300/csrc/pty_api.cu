@@ -12,6 +12,7 @@
 #include "../../include/pty.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -88,14 +89,18 @@ __global__ void k_iota(int* p, int n) {
     p[i] = i;
 }
 
-// Greedy first-fit grouping.  Boxes with corners a, b overlap iff
-// |a.y - b.y| < W and |a.x - b.x| < W; only the 3x3 neighbouring cells of a
-// W-sized grid can hold an overlapping corner.
+// Boxes with corners a, b overlap iff |a.y - b.y| < W and |a.x - b.x| < W;
+// only the 3x3 neighbouring cells of a W-sized grid can hold such a corner.
+int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
 // First-fit grouping in scan order into groups of pairwise-disjoint W x W
-// boxes.  Two corners in the same W x W cell of a grid always overlap, so a
-// group holds at most one member per cell: each group keeps a cell table and
-// a position tests at most the 3 x 3 cells around its own in each group it
-// tries.
+// boxes.  Exact tests use a per-group table over a W-sized grid (two corners
+// in one W x W cell always overlap, so a group holds at most one member per
+// cell: 3 x 3 lookups).  A finer grid (cells of W/4) keeps, per cell, a
+// bitset of the groups whose clash zone (|dy| < W and |dx| < W around a
+// member) covers the whole cell: those groups certainly clash, so a position
+// exact-tests only the groups whose bit is clear, in order.  The result is
+// the plain first fit.
 void greedy_group(const std::vector<int2>& c, int W, const int32_t* order,
                   int max_group, std::vector<int>& gptr, std::vector<int>& gpos) {
   const int N = (int)c.size();
@@ -106,40 +111,72 @@ void greedy_group(const std::vector<int2>& c, int W, const int32_t* order,
     if (j == 0 || c[j].x > maxy) maxy = c[j].x;
     if (j == 0 || c[j].y > maxx) maxx = c[j].y;
   }
+  // W grid: one member per group and cell (exact tests)
   const int ncy = (maxy - miny) / W + 1, ncx = (maxx - minx) / W + 1;
   const size_t ncell = (size_t)ncy * ncx;
-  std::vector<int> table;  // [group][cell] -> member index or -1
+  // fine grid: per cell, the groups whose clash zone covers the whole cell
+  const int s = std::max(1, W / 4);
+  const int nfy = (maxy - miny) / s + 1, nfx = (maxx - minx) / s + 1;
+  const size_t nfine = (size_t)nfy * nfx;
+  int words = 2;
+  std::vector<uint64_t> cover(nfine * words, 0);
+  std::vector<int> table;  // [group][cell] -> member or -1
   std::vector<int> gsize;
   std::vector<std::vector<int>> members;
   for (int n = 0; n < N; ++n) {
     const int j = order ? order[n] : n;
-    const int cy = (c[j].x - miny) / W, cx = (c[j].y - minx) / W;
+    const int jy = c[j].x, jx = c[j].y;
+    const int cy = (jy - miny) / W, cx = (jx - minx) / W;
+    const size_t f = (size_t)((jy - miny) / s) * nfx + (jx - minx) / s;
     const int G = (int)members.size();
-    int g = 0;
-    for (; g < G; ++g) {
-      if (max_group > 0 && gsize[g] >= max_group) continue;
-      const int* tg = table.data() + (size_t)g * ncell;
-      bool clash = false;
-      for (int dy = -1; dy <= 1 && !clash; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int yy = cy + dy, xx = cx + dx;
-          if (yy < 0 || xx < 0 || yy >= ncy || xx >= ncx) continue;
-          const int i = tg[(size_t)yy * ncx + xx];
-          if (i >= 0 && std::abs(c[i].x - c[j].x) < W && std::abs(c[i].y - c[j].y) < W) {
-            clash = true;
-            break;
+    int pick = G;
+    const uint64_t* cv = cover.data() + f * words;
+    for (int w = 0; w < words && pick == G; ++w) {
+      uint64_t free_ = ~cv[w];
+      while (free_) {
+        const int g = w * 64 + __builtin_ctzll(free_);
+        free_ &= free_ - 1;
+        if (g >= G) break;
+        if (max_group > 0 && gsize[g] >= max_group) continue;
+        const int* tg = table.data() + (size_t)g * ncell;
+        bool clash = false;
+        for (int dy = -1; dy <= 1 && !clash; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int yy = cy + dy, xx = cx + dx;
+            if (yy < 0 || xx < 0 || yy >= ncy || xx >= ncx) continue;
+            const int i = tg[(size_t)yy * ncx + xx];
+            if (i >= 0 && std::abs(c[i].x - jy) < W && std::abs(c[i].y - jx) < W) {
+              clash = true;
+              break;
+            }
           }
-        }
-      if (!clash) break;
+        if (!clash) { pick = g; break; }
+      }
     }
-    if (g == G) {
+    if (pick == G) {
+      if (G == words * 64) {
+        std::vector<uint64_t> c2(nfine * words * 2, 0);
+        for (size_t q = 0; q < nfine; ++q)
+          std::copy(cover.begin() + q * words, cover.begin() + (q + 1) * words, c2.begin() + q * words * 2);
+        cover.swap(c2);
+        words *= 2;
+      }
       members.emplace_back();
       gsize.push_back(0);
       table.resize(table.size() + ncell, -1);
     }
+    const int g = pick;
     members[g].push_back(j);
     ++gsize[g];
     table[(size_t)g * ncell + (size_t)cy * ncx + cx] = j;
+    // fine cells wholly inside j's clash zone (iy - W, iy + W) x (ix - W, ix + W)
+    const int fy0 = std::max(0, -floordiv(-(jy - W + 1 - miny), s));
+    const int fy1 = std::min(nfy - 1, floordiv(jy + W - s - miny, s));
+    const int fx0 = std::max(0, -floordiv(-(jx - W + 1 - minx), s));
+    const int fx1 = std::min(nfx - 1, floordiv(jx + W - s - minx, s));
+    const uint64_t bit = 1ull << (g & 63);
+    for (int fy = fy0; fy <= fy1; ++fy)
+      for (int fx = fx0; fx <= fx1; ++fx) cover[((size_t)fy * nfx + fx) * words + (g >> 6)] |= bit;
   }
   gptr.assign(members.size() + 1, 0);
   gpos.clear();
