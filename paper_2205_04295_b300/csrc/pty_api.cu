@@ -1240,9 +1240,16 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
     return fail(PTY_EINVAL, "tiling needs too much shared memory");
   // the registration passes take the same geometry where it fits their extra
   // crop plane, and the same patches per chunk
-  pty::Tiling nr = pty::make_tiling(W, M, true, 512, t->R, t->ppc, t->CB);
+  // (the extra plane can push the column pass past two CTAs per SM: halve
+  // its column block until two fit)
+  int cbr = t->CB;
+  pty::Tiling nr = pty::make_tiling(W, M, true, 512, t->R, t->ppc, cbr);
+  while (cbr > 2 && 2 * (nr.smB + 1024) > (size_t)pty::smem_per_sm()) {
+    cbr /= 2;
+    nr = pty::make_tiling(W, M, true, 512, t->R, t->ppc, cbr);
+  }
   if (t->ppcb > 0) nr.ppcb = t->ppcb;
-  if ((t->R && (M + 1) * t->R * L > 256) || (t->CB && (M + 1) * t->CB * L > 384) ||
+  if ((t->R && (M + 1) * t->R * L > 256) ||
       nr.smA > 227 * 1024 || nr.smB > 227 * 1024 || nr.smC > 227 * 1024)
     nr = h->tlr;
   const size_t W2 = (size_t)W * W;

@@ -47,7 +47,7 @@ __device__ __noinline__ void batch_cols(const BatchProb& pb, const BatchTask& tk
   const int* ids = pb.gpos + tk.ids_off;
   for (int bx = tk.x0; bx < tk.x1; ++bx) {
     cols_body<W, CB, false, false>(pb.scratch, pb.M, pb.I, ids, pb.tw, pb.inv_w, pb.a.eps,
-                                   pb.err_part, pb.M, 0, 1, tk.npatch, bx, tk.y);
+                                   pb.err_part, pb.M, 1, tk.npatch, bx, tk.y);
     __syncthreads();
   }
 }
@@ -148,7 +148,7 @@ k_batch(const BatchProb* __restrict__ probs, const BatchTask* __restrict__ tasks
 
 size_t batch_smem(const Tiling& t) {
   // the batched column pass reads straight into registers: no stage
-  const size_t smB = t.smB - (size_t)(t.M + t.xo) * t.W * t.CB * sizeof(float2);
+  const size_t smB = t.smB - (size_t)t.M * t.W * t.CB * sizeof(float2);
   return std::max({t.smA, smB, t.smC, (size_t)256 * sizeof(double)});  // 256: the error reduction
 }
 

@@ -32,6 +32,8 @@ bool supported_W(int W);
 // Every kernel's opt-in limit is set to this value: the attribute is global
 // per kernel function, so a limit sized for one tiling would reject another.
 int smem_optin();
+// Shared memory per SM (bytes).
+int smem_per_sm();
 // Let `func` use all dynamic shared memory the device allows beside its own
 // static shared memory.
 cudaError_t allow_max_smem(const void* func);
@@ -102,6 +104,7 @@ cudaError_t launch_cols_intensity(const Tiling& t, const float2* scratch,
 struct RefGeo {
   int W, U, K;   // fine grid K = ceil(1.5 U) points per axis
   int CBX, RX;   // columns / rows per CTA of the correlation passes
+  int RB;        // rows of X per CTA of the upsampled matrix DFT
   size_t smX, smR, smU;
 };
 RefGeo make_refgeo(int W, int U);

@@ -133,7 +133,7 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
 }
 
 // ---------------------------------------------------------------- pass B
-// Request (cp.async) the column block [c0, c0 + CB) of the MA planes of patch
+// Request (cp.async) the column block [c0, c0 + CB) of the MA mode planes of patch
 // slot lp into `stage` ([plane][row][column]) and the block's counts into
 // `cnt` ([row][column], rows and columns fftshifted, DC at the centre of the
 // stored pattern).  CB is even, so every segment is 16-byte aligned.
@@ -180,14 +180,13 @@ template <int W, int CB, bool GRAD, bool STAGE = true>
 PTY_D void cols_body(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part, int npl, int xo, int ppcb, int npatch, int bx, int by) {
+       float* __restrict__ err_part, int npl, int ppcb, int npatch, int bx, int by) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
-  const int MA = M + xo;
   float2* tw = reinterpret_cast<float2*>(smem4);
-  float2* stage = tw + W;                                        // MA x W x CB
-  float2* tbuf = stage + (STAGE ? MA * W * CB : 0);              // MA x CB lines
-  float* Sb = reinterpret_cast<float*>(tbuf + MA * CB * G::LP);  // M x W x CB
+  float2* stage = tw + W;                                        // M x W x CB
+  float2* tbuf = stage + (STAGE ? M * W * CB : 0);               // M x CB lines
+  float* Sb = reinterpret_cast<float*>(tbuf + M * CB * G::LP);   // M x W x CB
   uint16_t* cnt = reinterpret_cast<uint16_t*>(Sb + M * CB * W);  // 2 x W x CB
   __shared__ float red[32];
 
@@ -195,16 +194,14 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
   const int c0 = bx * CB;
   const int c = threadIdx.x % CB, rest = threadIdx.x / CB;
   const int lane = rest % G::L, k = rest / G::L;
-  // k < M: the modes; k == M (with xo): the crop, forward transform only
-  const bool act = k < MA;
-  const bool mode = k < M;
+  const bool act = k < M;  // thread of mode k's line for column c
   const int kk0 = act ? k : 0;
   float2* lbuf = tbuf + (kk0 * CB + c) * G::LP;
   const float2* srow = stage + kk0 * W * CB + c;
   const int nw = (blockDim.x + 31) >> 5;
   const int p0 = by * ppcb, p1 = min(npatch, p0 + ppcb);
   if constexpr (STAGE) {
-    if (p0 < p1) cols_stage<W, CB>(scratch, I, ids[p0], p0, npl, MA, c0, stage, cnt);
+    if (p0 < p1) cols_stage<W, CB>(scratch, I, ids[p0], p0, npl, M, c0, stage, cnt);
     cp_async_commit();
   }
   for (int lp = p0; lp < p1; ++lp) {
@@ -222,7 +219,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
       }
       __syncthreads();  // the stage is free: request the next patch
       if (lp + 1 < p1)
-        cols_stage<W, CB>(scratch, I, ids[lp + 1], lp + 1, npl, MA, c0, stage,
+        cols_stage<W, CB>(scratch, I, ids[lp + 1], lp + 1, npl, M, c0, stage,
                           cnt + ((lp + 1 - p0) & 1) * W * CB);
       cp_async_commit();
     } else {
@@ -246,14 +243,8 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
     float2 z[G::N2];
     if (act && lane < G::N1) {
       fwd_step3<W>(z, lane, lbuf);
-      if (mode) {
 #pragma unroll
-        for (int k2 = 0; k2 < G::N2; ++k2)
-          Sb[(k * W + lane + G::N1 * k2) * CB + c] = cabs2(z[k2]);
-      } else {
-#pragma unroll
-        for (int k2 = 0; k2 < G::N2; ++k2) col[(size_t)(lane + G::N1 * k2) * W] = z[k2];
-      }
+      for (int k2 = 0; k2 < G::N2; ++k2) Sb[(k * W + lane + G::N1 * k2) * CB + c] = cabs2(z[k2]);
     }
     __syncthreads();
     // constraint factor once per detector pixel (u, c): S = sum_k |Psi_k|^2 in a
@@ -288,14 +279,14 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
       for (int i = 0; i < nw; ++i) t += red[i];  // fixed order
       err_part[(size_t)j * (W / CB) + bx] = t;
     }
-    if (mode && lane < G::N1) {
+    if (act && lane < G::N1) {
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2)
         z[k2] = cscale(z[k2], Sb[(lane + G::N1 * k2) * CB + c]);
       inv_stepA<W>(z, lane, tw, lbuf);
     }
     __syncthreads();
-    if (mode && lane < G::N2) {
+    if (act && lane < G::N2) {
       float2 v[G::N1];
       inv_stepB<W>(v, lane, lbuf);
 #pragma unroll

@@ -4,10 +4,11 @@
 // Opt. Lett. 33, 156, 2008).
 //
 // For each patch of a group, after pass C, the scratch holds
-//   plane M     : A = F(o_j)            (crop before the update; passes A, B)
+//   plane M     : row DFTs of o_j       (crop before the update; pass A)
 //   plane M + 1 : row DFTs of o'_j      (refined crop; pass C)
-// xcorr_cols : column DFTs of plane M+1 -> B = F(o'_j); X = B conj(A) is stored
-//              in plane M; inverse column DFTs of X into plane M+1.
+// xcorr_cols : column DFTs of both planes -> A = F(o_j), B = F(o'_j);
+//              X = B conj(A) is stored in plane M; inverse column DFTs of X
+//              into plane M+1.
 // xcorr_rows : inverse row DFTs of plane M+1 -> c = F^-1 X (unnormalised);
 //              per row block the largest |c|^2 and its first row-major index.
 // updft      : coarse peak (s_y, s_x) wrapped to [-W/2, W/2); the
@@ -20,6 +21,7 @@
 // The phase of every matrix-DFT entry is an exact integer multiple of
 // 2 pi / (U W): entry (v, k) of E_c is root[(v_s (U s_x + k - K/2)) mod (U W)]
 // with v_s the signed frequency; the roots come from a host table.
+#include "pty_copy.cuh"
 #include "pty_fft.cuh"
 #include "pty_internal.h"
 
@@ -84,13 +86,24 @@ k_xcorr_cols(float2* __restrict__ scratch, int npl, int M, int CB,
   float2* colA = scratch + ((size_t)lp * npl + M) * W * W + c0 + c;
   float2* colB = colA + (size_t)W * W;
   float2* lbuf = tbuf + c * G::LP;
-  __syncthreads();
-  float2 v[G::N1];
+  // both columns are requested together
+  float2 v[G::N1], vb[G::N1];
   if (act && lane < G::N2) {
 #pragma unroll
-    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = colB[(size_t)(G::N2 * n1 + lane) * W];
-    fwd_step1<W>(v, lane, tw, lbuf);
+    for (int n1 = 0; n1 < G::N1; ++n1) {
+      v[n1] = colA[(size_t)(G::N2 * n1 + lane) * W];
+      vb[n1] = colB[(size_t)(G::N2 * n1 + lane) * W];
+    }
   }
+  __syncthreads();
+  // A = F(o_j): the column DFTs of plane M (its row DFTs come from pass A)
+  if (act && lane < G::N2) fwd_step1<W>(v, lane, tw, lbuf);
+  __syncthreads();
+  float2 za[G::N2];
+  if (act && lane < G::N1) fwd_step3<W>(za, lane, lbuf);
+  __syncthreads();
+  // B = F(o'_j)
+  if (act && lane < G::N2) fwd_step1<W>(vb, lane, tw, lbuf);
   __syncthreads();
   float2 z[G::N2];
   if (act && lane < G::N1) {
@@ -98,7 +111,7 @@ k_xcorr_cols(float2* __restrict__ scratch, int npl, int M, int CB,
 #pragma unroll
     for (int k2 = 0; k2 < G::N2; ++k2) {
       const size_t u = lane + G::N1 * k2;
-      const float2 X = cmulc(z[k2], colA[u * W]);  // B conj(A)
+      const float2 X = cmulc(z[k2], za[k2]);  // B conj(A)
       colA[u * W] = X;
       z[k2] = X;
     }
@@ -157,14 +170,15 @@ k_xcorr_rows(const float2* __restrict__ scratch, int npl, int M, int RX,
 
 // ------------------------------------------------------------ updft
 // The fine grid is evaluated as c_up = E_r X E_c in two kernels:
-//   updft_part : CTA (row block of RU rows of X, patch): T = X_rows E_c
-//                (RU x K) and the block's share E_r[:, rows] T (K x K),
+//   updft_part : CTA (row block of RB rows of X, patch): T = X_rows E_c
+//                (RB x K) and the block's share E_r[:, rows] T (K x K),
 //                written as a partial sum;
 //   updft_final: per patch, the partial sums added in block order, |c_up|^2,
 //                first maximum in row-major order -> shift.
 // The phase of every entry is an exact multiple of 2 pi / (U W), read from
-// the root table staged in shared memory.
-constexpr int RU = 16;
+// the root table staged in shared memory.  T is register-tiled: a thread
+// accumulates 2 rows x 4 fine-grid columns, and the 32 threads of a warp
+// share the columns, so each root lookup is a broadcast.
 
 PTY_D void coarse_peak(const float* cval, const int* cidx, int lp, int nparts, int W,
                        int& sy, int& sx, float* rv, int* ri) {
@@ -177,62 +191,95 @@ PTY_D void coarse_peak(const float* cval, const int* cidx, int lp, int nparts, i
   sx = wrap_shift(bi % W, W);
 }
 
+// acc += a b, complex, as four fused multiply-adds
+PTY_D void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
 template <int W>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_updft_part(const float2* __restrict__ scratch, int npl, int M, int nparts,
              const float* __restrict__ cval, const int* __restrict__ cidx,
-             const float2* __restrict__ roots_g, int U, int K, float2* __restrict__ part) {
+             const float2* __restrict__ roots_g, int U, int K, int RB,
+             float2* __restrict__ part) {
   extern __shared__ float4 smem4[];
   const int UW = U * W;
   constexpr int XP = W + 1;                  // padded row pitch of the X block
-  float2* roots = reinterpret_cast<float2*>(smem4);
-  float2* Xs = roots + UW;                   // [RU][W + 1]
-  float2* T = Xs + RU * XP;                  // [RU][K]
+  const int KP = (K + 3) / 4 * 4;            // columns padded to whole tiles
+  float2* E = reinterpret_cast<float2*>(smem4);  // [W][KP]: this patch's E_c
+  float2* Xs = E + W * KP;                   // [RB][W + 1]
+  float2* T = Xs + RB * XP;                  // [RB][KP]
+  float2* Er = T + RB * KP;                  // [K][RB]: this block's E_r columns
   __shared__ float rv[32];
   __shared__ int ri[32];
-  const int lp = blockIdx.y, u0 = blockIdx.x * RU;
-  for (int e = threadIdx.x; e < UW; e += blockDim.x) roots[e] = roots_g[e];
+  const int lp = blockIdx.y, u0 = blockIdx.x * RB;
   const float2* X = scratch + ((size_t)lp * npl + M) * W * W + (size_t)u0 * W;
-  for (int e = threadIdx.x; e < RU * W; e += blockDim.x) {
+  // all staging is asynchronous (cp.async): no thread waits on a load
+  // before issuing the next one
+  for (int e = threadIdx.x; e < RB * W; e += blockDim.x) {
     const int r = e / W, v = e - r * W;
-    Xs[r * XP + v] = X[(size_t)r * W + v];
+    cp_async<8>(Xs + r * XP + v, X + (size_t)r * W + v);
   }
   int sy, sx;
   coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);  // contains barriers
   const int half = K / 2;
-  // T[r][k] = sum_v X[u0 + r][v] root[(v_s (U sx + k - half)) mod UW]
-  // lanes of a half-warp: 16 rows sharing one k (one root index per step)
-  for (int q = threadIdx.x; q < RU * K; q += blockDim.x) {
-    const int k = q / RU, r = q - k * RU;
-    const int a = modp((long long)U * sx + k - half, UW);
-    const float2* xr = Xs + r * XP;
-    float2 acc = make_float2(0.f, 0.f);
-    int n = 0;
-    for (int v = 0; v < W / 2; ++v) {
-      acc = cadd(acc, cmul(xr[v], roots[n]));
-      n += a;
-      if (n >= UW) n -= UW;
+  // E[v][k] = root[(v_s (U sx + k - half)) mod UW]: a thread fills one column
+  // over a run of 32 frequencies (runs never straddle v = W/2), stepping the
+  // index instead of reducing a product per entry
+  for (int t = threadIdx.x; t < KP * (W / 32 + (W % 32 != 0)); t += blockDim.x) {
+    const int k = t % KP, v0 = (t / KP) * 32, v1 = min(W, v0 + 32);
+    const int a = modp((long long)U * sx + min(k, K - 1) - half, UW);
+    int n = -1;
+    for (int v = v0; v < v1; ++v) {
+      if (n < 0 || v == W / 2) {
+        n = modp((long long)(v < W / 2 ? v : v - W) * a, UW);
+      } else {
+        n += a;
+        if (n >= UW) n -= UW;
+      }
+      cp_async<8>(E + v * KP + k, roots_g + n);
     }
-    n = modp(-(long long)(W / 2) * a, UW);
-    for (int v = W / 2; v < W; ++v) {
-      acc = cadd(acc, cmul(xr[v], roots[n]));
-      n += a;
-      if (n >= UW) n -= UW;
+  }
+  for (int t = threadIdx.x; t < K * RB; t += blockDim.x) {
+    const int k1 = t / RB, r = t - k1 * RB, u = u0 + r;
+    const int b = modp((long long)U * sy + k1 - half, UW);
+    cp_async<8>(Er + t, roots_g + modp((long long)(u < W / 2 ? u : u - W) * b, UW));
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  // T[r][k] = sum_v X[u0 + r][v] E[v][k]; a thread holds 1 row x 4 columns,
+  // a warp 32 rows of the same columns (E reads are broadcasts)
+  const int nkt = KP / 4;
+  for (int tile = threadIdx.x; tile < RB * nkt; tile += blockDim.x) {
+    const int r0 = tile % RB, k0 = 4 * (tile / RB);
+    float2 c0[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c0[q] = make_float2(0.f, 0.f);
+    const float2* x0 = Xs + r0 * XP;
+    const float4* ev = reinterpret_cast<const float4*>(E + k0);
+#pragma unroll 4
+    for (int v = 0; v < W; ++v) {
+      const float2 p0 = x0[v];
+      const float4 ea = ev[(v * KP) / 2], eb = ev[(v * KP) / 2 + 1];
+      cfma(c0[0], p0, make_float2(ea.x, ea.y));
+      cfma(c0[1], p0, make_float2(ea.z, ea.w));
+      cfma(c0[2], p0, make_float2(eb.x, eb.y));
+      cfma(c0[3], p0, make_float2(eb.z, eb.w));
     }
-    T[r * K + k] = acc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) T[r0 * KP + k0 + q] = c0[q];
   }
   __syncthreads();
-  // share of this row block: sum_{r} root[(u_s (U sy + k1 - half)) mod UW] T[r][k2]
+  // share of this row block: sum_{r} E_r[k1][u0 + r] T[r][k2]
   float2* dst = part + ((size_t)lp * gridDim.x + blockIdx.x) * K * K;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int k1 = e / K, k2 = e - k1 * K;
-    const int b = modp((long long)U * sy + k1 - half, UW);
     float2 acc = make_float2(0.f, 0.f);
-    for (int r = 0; r < RU; ++r) {
-      const int u = u0 + r;
-      const int us = u < W / 2 ? u : u - W;
-      acc = cadd(acc, cmul(roots[modp((long long)us * b, UW)], T[r * K + k2]));
-    }
+    for (int r = 0; r < RB; ++r) cfma(acc, Er[k1 * RB + r], T[r * KP + k2]);
     dst[e] = acc;
   }
 }
@@ -361,7 +408,12 @@ RefGeo make_refgeo(int W, int U) {
     case 192: refgeo_fill<192>(g); break;
     default: refgeo_fill<256>(g); break;
   }
-  g.smU = (size_t)(g.U * W + RU * (W + 1) + RU * g.K) * sizeof(float2);
+  // the most X rows per CTA (64, 32 or 16, at most W/2) whose tables fit
+  const int KP = (g.K + 3) / 4 * 4;
+  for (g.RB = std::min(64, std::max(16, W / 2)); ; g.RB /= 2) {
+    g.smU = (size_t)(W * KP + g.RB * (W + 1) + g.RB * KP + g.K * g.RB) * sizeof(float2);
+    if (g.smU <= (size_t)smem_optin() - 1024 || g.RB <= 16) break;
+  }
   return g;
 }
 
@@ -419,9 +471,9 @@ cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const
     k_coarse_only<<<npatch, 128, 0, s>>>(ids, nparts, g.W, cval, cidx, shift, gap);
     return cudaGetLastError();
   }
-  const int nblocks = g.W / RU;
-  PTY_DISPATCH_W(g.W, (k_updft_part<WW><<<dim3(nblocks, npatch), 256, g.smU, s>>>(
-                          scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K, part)));
+  const int nblocks = g.W / g.RB;
+  PTY_DISPATCH_W(g.W, (k_updft_part<WW><<<dim3(nblocks, npatch), 512, g.smU, s>>>(
+                          scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K, g.RB, part)));
   k_updft_final<<<npatch, 256, 0, s>>>(ids, g.W, nblocks, nparts, cval, cidx, g.U, g.K, part,
                                        shift, gap);
   return cudaGetLastError();

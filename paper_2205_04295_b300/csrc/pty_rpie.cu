@@ -27,8 +27,8 @@ __global__ void __launch_bounds__(384, 2)
 k_cols(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part, int npl, int xo, int ppcb, int npatch) {
-  cols_body<W, CB, GRAD>(scratch, M, I, ids, tw_g, inv_w, eps, err_part, npl, xo, ppcb, npatch,
+       float* __restrict__ err_part, int npl, int ppcb, int npatch) {
+  cols_body<W, CB, GRAD>(scratch, M, I, ids, tw_g, inv_w, eps, err_part, npl, ppcb, npatch,
                          blockIdx.x, blockIdx.y);
 }
 
@@ -227,6 +227,16 @@ template <int W> void geo(int& L, int& LP) {
 
 }  // namespace
 
+int smem_per_sm() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 228 * 1024;
+  }
+  return v;
+}
+
 int smem_optin() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -314,16 +324,18 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   t.R = R;
   t.ppc = ppc_req > 0 ? ppc_req : 4;
   t.ppcb = 2;
-  int CB = pow2_floor(std::max(1, max_threads_b / (MA * L)));
-  CB = std::max(2, std::min(16, CB));  // MA * CB * L <= max_threads_b threads
+  int CB = pow2_floor(std::max(1, max_threads_b / (M * L)));
+  CB = std::max(2, std::min(16, CB));  // M * CB * L <= max_threads_b threads
   while ((W / 2) % CB) CB /= 2;
   if (CB_req > 0) CB = CB_req;
   t.CB = CB;
   t.thrA = round32(MA * R * L);
   t.thrC = round32(M * R * L);
-  t.thrB = round32(MA * CB * L);
+  t.thrB = round32(M * CB * L);
   t.smA = (size_t)(W + M * R * W + MA * R * LP + 2 * R * W) * sizeof(float2);
-  t.smB = (size_t)(W + MA * W * CB + MA * CB * LP) * sizeof(float2) +
+  // pass B transforms the M modes only (the crop plane's column DFTs are
+  // taken by the registration's correlation pass)
+  t.smB = (size_t)(W + M * W * CB + M * CB * LP) * sizeof(float2) +
           (size_t)M * CB * W * sizeof(float) + (size_t)2 * W * CB * sizeof(uint16_t);
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
@@ -391,7 +403,7 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, (k_cols<WW, CBB, false><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, I, ids, tw, inv_w, eps, err_part, t.npl, t.xo, t.ppcb,
+                          scratch, t.M, I, ids, tw, inv_w, eps, err_part, t.npl, t.ppcb,
                           npatch))));
   return cudaGetLastError();
 }
@@ -402,7 +414,7 @@ cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, (k_cols<WW, CBB, true><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, I, ids, tw, inv_w, delta, loss_part, npl, 0, t.ppcb,
+                          scratch, t.M, I, ids, tw, inv_w, delta, loss_part, npl, t.ppcb,
                           npatch))));
   return cudaGetLastError();
 }
