@@ -14,6 +14,7 @@
 //   grad_rows_fwd -> cols<GRAD> -> grad_rows_inv -> grad_scatter
 // per chunk of a group of positions whose (W+1)-boxes are pairwise disjoint,
 // so the scatter of dL/dO needs no atomics and is deterministic.
+#include "pty_copy.cuh"
 #include "pty_fft.cuh"
 #include "pty_internal.h"
 
@@ -28,14 +29,22 @@ PTY_D float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-PTY_D float block_sum(float v, float* red) {
+// Block-wide sums of two values at once; every thread gets them.  Contains barriers.
+PTY_D float2 block_sum2(float2 v, float* red) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  v = warp_sum(v);
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
   __syncthreads();
-  if (l == 0) red[w] = v;
+  if (l == 0) {
+    red[2 * w] = v.x;
+    red[2 * w + 1] = v.y;
+  }
   __syncthreads();
-  float t = 0.f;
-  for (int i = 0; i < nw; ++i) t += red[i];
+  float2 t = make_float2(0.f, 0.f);
+  for (int i = 0; i < nw; ++i) {  // fixed order
+    t.x += red[2 * i];
+    t.y += red[2 * i + 1];
+  }
   return t;
 }
 
@@ -53,11 +62,24 @@ PTY_D Bil bil_of(const float* pos, int j) {
   return b;
 }
 
-// o(r, c) and its derivatives from the four neighbours (row-major O).
-PTY_D void bil_sample(const float2* O, int Hx, const Bil& b, int r, int c, float2& o,
+// Request (cp.async) the R + 1 object rows iy + r0 .. iy + r0 + R, columns
+// ix .. ix + W, that the bilinear crop rows r0 .. r0 + R - 1 of a patch read.
+template <int W>
+PTY_D void grad_stage(const float2* O, int Hx, const Bil& b, int R, int r0, float2* st) {
+  constexpr int SP = W + 1;
+  for (int e = threadIdx.x; e < (R + 1) * SP; e += blockDim.x) {
+    const int q = e / SP, c = e - q * SP;
+    cp_async<8>(st + e, O + (size_t)(b.iy + r0 + q) * Hx + b.ix + c);
+  }
+}
+
+// o(r, c) and its derivatives from the staged rows (pitch W + 1).
+template <int W>
+PTY_D void bil_staged(const float2* st, const Bil& b, int r, int c, float2& o,
                       float2* dy = nullptr, float2* dx = nullptr) {
-  const float2* p = O + (size_t)(b.iy + r) * Hx + b.ix + c;
-  const float2 q00 = p[0], q01 = p[1], q10 = p[Hx], q11 = p[Hx + 1];
+  constexpr int SP = W + 1;
+  const float2* p = st + r * SP + c;
+  const float2 q00 = p[0], q01 = p[1], q10 = p[SP], q11 = p[SP + 1];
   const float wy0 = 1.f - b.fy, wy1 = b.fy, wx0 = 1.f - b.fx, wx1 = b.fx;
   o.x = wy0 * (wx0 * q00.x + wx1 * q01.x) + wy1 * (wx0 * q10.x + wx1 * q11.x);
   o.y = wy0 * (wx0 * q00.y + wx1 * q01.y) + wy1 * (wx0 * q10.y + wx1 * q11.y);
@@ -70,6 +92,9 @@ PTY_D void bil_sample(const float2* O, int Hx, const Bil& b, int r, int c, float
 }
 
 // ---------------------------------------------------- forward rows
+// The next patch's object rows are requested while the current patch is
+// transformed; the crop rows are interpolated once per patch (not once per
+// mode).
 template <int W>
 __global__ void __launch_bounds__(256)
 k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
@@ -77,32 +102,46 @@ k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__
                 int npatch, const float2* __restrict__ tw_g, float2* __restrict__ scratch,
                 int npl) {
   using G = Line<W>;
+  constexpr int SP = W + 1;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* Prow = tw + W;
   float2* tbuf = Prow + M * R * W;
+  float2* obuf = tbuf + M * R * G::LP;  // R x W interpolated crop rows
+  float2* st = obuf + R * W;            // 2 x (R + 1) x (W + 1) object rows
   const int r0 = blockIdx.x * R;
+  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  if (p0 < p1) grad_stage<W>(O, Hx, bil_of(pos, ids[p0]), R, r0, st);
+  cp_async_commit();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
     Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
   }
-  __syncthreads();
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
   const bool act = line < M * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
-  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
   for (int lp = p0; lp < p1; ++lp) {
     const Bil b = bil_of(pos, ids[lp]);
+    const float2* sc = st + ((lp - p0) & 1) * (R + 1) * SP;
+    cp_async_wait<0>();
+    __syncthreads();  // this patch's rows have landed; obuf and lbuf are free
+    if (lp + 1 < p1)
+      grad_stage<W>(O, Hx, bil_of(pos, ids[lp + 1]), R, r0,
+                    st + ((lp + 1 - p0) & 1) * (R + 1) * SP);
+    cp_async_commit();
+    for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+      const int rr = e / W, c = e - rr * W;
+      bil_staged<W>(sc, b, rr, c, obuf[e]);
+    }
+    __syncthreads();
     if (act && lane < G::N2) {
       float2 v[G::N1];
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
-        float2 o;
-        bil_sample(O, Hx, b, r0 + r, c, o);
-        v[n1] = cmul(Prow[(k * R + r) * W + c], o);
+        v[n1] = cmul(Prow[(k * R + r) * W + c], obuf[r * W + c]);
       }
       fwd_step1<W>(v, lane, tw, lbuf);
     }
@@ -114,11 +153,13 @@ k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
     }
-    __syncthreads();
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------- inverse rows + adjoint
+// The object rows of the next patch are requested while the current patch
+// is transformed (the far-field rows are read straight into registers).
 template <int W>
 __global__ void __launch_bounds__(256)
 k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
@@ -127,29 +168,37 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
                 const float2* __restrict__ tw_g, float2* __restrict__ gP_part, int accumulate,
                 float* __restrict__ gpos_part) {
   using G = Line<W>;
+  constexpr int SP = W + 1;
   extern __shared__ float4 smem4[];
   const int TB = max(M * R * G::LP, M * R * W);
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* Prow = tw + W;
   float2* tbuf = Prow + M * R * W;  // transpose buffer, then conj(P) G_psi terms
   float2* gp = tbuf + TB;           // dL/dP partial sums of this CTA
-  __shared__ float red[32];
+  float2* obuf = gp + M * R * W;    // R x W interpolated crop rows
+  float2* st = obuf + R * W;        // 2 x (R + 1) x (W + 1) object rows
+  __shared__ float red2[64];
   const int r0 = blockIdx.x * R, nrb = W / R;
+  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  auto stage = [&](int q, float2* stq) { grad_stage<W>(O, Hx, bil_of(pos, ids[q]), R, r0, stq); };
+  if (p0 < p1) stage(p0, st);
+  cp_async_commit();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
     Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
     gp[e] = make_float2(0.f, 0.f);
   }
-  __syncthreads();
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
   const bool act = line < M * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
-  const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
   for (int lp = p0; lp < p1; ++lp) {
     const int j = ids[lp];
     const Bil b = bil_of(pos, j);
+    const float2* sc = st + ((lp - p0) & 1) * (R + 1) * SP;
+    cp_async_wait<0>();
+    __syncthreads();  // this patch's rows have landed
     if (act && lane < G::N1) {
       const float2* src = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
       float2 z[G::N2];
@@ -157,7 +206,13 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
       for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
       inv_stepA<W>(z, lane, tw, lbuf);
     }
-    __syncthreads();
+    for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
+      const int rr = e / W, c = e - rr * W;
+      bil_staged<W>(sc, b, rr, c, obuf[e]);
+    }
+    __syncthreads();  // request the next patch's object rows
+    if (lp + 1 < p1) stage(lp + 1, st + ((lp + 1 - p0) & 1) * (R + 1) * SP);
+    cp_async_commit();
     float2 v[G::N1];
     if (act && lane < G::N2) inv_stepB<W>(v, lane, lbuf);
     __syncthreads();
@@ -165,8 +220,7 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
-        float2 o;
-        bil_sample(O, Hx, b, r0 + r, c, o);
+        const float2 o = obuf[r * W + c];
         const float2 Pk = Prow[(k * R + r) * W + c];
         gp[(k * R + r) * W + c] = cadd(gp[(k * R + r) * W + c], cmulc(v[n1], o));  // conj(o) G_psi
         tbuf[(k * R + r) * W + c] = cmulc(v[n1], Pk);                              // conj(P) G_psi
@@ -180,19 +234,19 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
       float2 g = make_float2(0.f, 0.f);
       for (int kk = 0; kk < M; ++kk) g = cadd(g, tbuf[(kk * R + rr) * W + c]);
       float2 o, dy, dx;
-      bil_sample(O, Hx, b, r0 + rr, c, o, &dy, &dx);
+      bil_staged<W>(sc, b, rr, c, o, &dy, &dx);
       gy += g.x * dy.x + g.y * dy.y;  // Re(conj(G_o) do/dy)
       gx += g.x * dx.x + g.y * dx.y;
       gout[(size_t)rr * W + c] = g;
     }
-    gy = block_sum(gy, red);
-    gx = block_sum(gx, red);
+    const float2 gs = block_sum2(make_float2(gy, gx), red2);
     if (threadIdx.x == 0) {
-      gpos_part[((size_t)j * nrb + blockIdx.x) * 2] = gy;
-      gpos_part[((size_t)j * nrb + blockIdx.x) * 2 + 1] = gx;
+      gpos_part[((size_t)j * nrb + blockIdx.x) * 2] = gs.x;
+      gpos_part[((size_t)j * nrb + blockIdx.x) * 2 + 1] = gs.y;
     }
-    __syncthreads();
   }
+  cp_async_wait<0>();
+  __syncthreads();
   const int slot = blockIdx.y;
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int kk = e / (R * W), rem = e - kk * R * W, rr = rem / W, c = rem - rr * W;
@@ -291,7 +345,22 @@ static size_t grad_inv_smem(const Tiling& t) {
     default: LP = Line<256>::LP; break;
   }
   const int TB = std::max(t.M * t.R * LP, t.M * t.R * t.W);
-  return (size_t)(t.W + t.M * t.R * t.W + TB + t.M * t.R * t.W) * sizeof(float2);
+  return (size_t)(t.W + t.M * t.R * t.W + TB + t.M * t.R * t.W + t.R * t.W +
+                  2 * (t.R + 1) * (t.W + 1)) * sizeof(float2);
+}
+
+static size_t grad_fwd_smem(const Tiling& t) {
+  int LP = 0;
+  switch (t.W) {
+    case 32: LP = Line<32>::LP; break;
+    case 64: LP = Line<64>::LP; break;
+    case 96: LP = Line<96>::LP; break;
+    case 128: LP = Line<128>::LP; break;
+    case 192: LP = Line<192>::LP; break;
+    default: LP = Line<256>::LP; break;
+  }
+  return (size_t)(t.W + t.M * t.R * t.W + t.M * t.R * LP + t.R * t.W +
+                  2 * (t.R + 1) * (t.W + 1)) * sizeof(float2);
 }
 
 cudaError_t set_grad_smem(const Tiling& t) {
@@ -309,7 +378,7 @@ cudaError_t launch_grad_rows_fwd(const Tiling& t, const float2* O, int Hx, const
                                  const float2* tw, float2* scratch, int npl, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
-  PTY_DISPATCH_W(t.W, (k_grad_rows_fwd<WW><<<grid, t.thrA, t.smA, s>>>(
+  PTY_DISPATCH_W(t.W, (k_grad_rows_fwd<WW><<<grid, t.thrC, grad_fwd_smem(t), s>>>(
                           O, Hx, P, t.M, t.R, t.ppc, ids, pos, npatch, tw, scratch, npl)));
   return cudaGetLastError();
 }
