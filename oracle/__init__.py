@@ -24,8 +24,12 @@ implementation of ptychography algorithms" (arXiv 2205.04295):
                       Eqs. 8-9; Kingma & Ba Algorithm 1).
 * ``grad``         -- amplitude loss of the bilinear-crop forward model and
                       its analytic gradient (differentiable form).
+* ``modes``        -- orthogonalisation of the probe modes through the
+                      eigendecomposition of their Gram matrix (mixed state
+                      of Eq. 4, after Thibault & Menzel 2013).
 
 Everything is complex128 / float64.  Library primitives used as steps:
-``numpy.fft`` (the DFT) and ``numpy.matmul`` (matrix DFT).  The oracle shares
+``numpy.fft`` (the DFT), ``numpy.matmul`` (matrix DFT) and
+``numpy.linalg.eigh`` (Hermitian eigendecomposition).  The oracle shares
 no code with the CUDA library and never imports it.
 """
