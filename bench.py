@@ -364,6 +364,14 @@ def run_ours(args, wl, rank, world, local):
     h2d = I_h.numel() * 2 + pos_h.numel() * 4 + O0_h.numel() * 8 + P0_h.numel() * 8
     d2h = O_out.numel() * 8 + P_out.numel() * 8
 
+    # ---- probe-mode orthogonalisation (between iterations; synchronises)
+    prob.orthogonalize_probe()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        prob.orthogonalize_probe()
+    ortho_ms = (time.perf_counter() - t0) / 5 * 1e3
+
     batch = run_batch_measure(args, dev) if not args.no_batch else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -393,6 +401,7 @@ def run_ours(args, wl, rank, world, local):
                              "what": "same schedule as stock torch ops + cuFFT (comparison form)"},
            "refine": {"value": world * wl.N / (refine_ms / 1e3), "unit": UNIT, "ms_per_step": refine_ms,
                       "what": "same step with XCORR_A registration (U = 20) and one Adam step per position"},
+           "orthogonalize_ms": ortho_ms,
            "e2e": {"value": world * wl.N * e2e_steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "clocks": clk.summary()}

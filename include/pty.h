@@ -273,6 +273,24 @@ int pty_batch_run(pty_batch* b, int n_iter, const pty_rpie_params* p);
 int pty_batch_status(pty_batch* b, int* per_problem);
 int pty_batch_destroy(pty_batch* b);
 
+/* Orthogonalise the probe modes in place (between iterations; the paper's
+ * mixed state, Eq. 4, after the multimode ePIE of Thibault & Menzel 2013):
+ * with the Gram matrix G_kl = sum_r conj(P_k(r)) P_l(r) = V diag(w) V^H
+ * (w decreasing), P'_m = sum_k V_km P_k.  The new modes are mutually
+ * orthogonal, sum_r |P'_m|^2 = w_m, and the density matrix
+ * sum_k P_k(r) conj(P_k(r')) is unchanged.  Each eigenvector's phase is fixed
+ * by making its largest-magnitude entry (the first on ties) real and
+ * positive.  G is reduced on the GPU in double precision, the M x M
+ * eigenproblem solved on the host (double, cyclic Jacobi), V applied on the
+ * GPU.  power_out (host, M doubles, may be NULL) receives w.  Synchronises. */
+int pty_orthogonalize_probe(pty_handle* h, double* power_out);
+
+/* Host-only Hermitian eigensolver used by pty_orthogonalize_probe (no GPU
+ * needed): A is M x M (M <= 16) complex, row-major, interleaved (re, im)
+ * doubles; w receives the eigenvalues in decreasing order, V (M x M, same
+ * layout) the eigenvectors as columns, phases fixed as above. */
+int pty_hermitian_eig(int M, const double* A, double* w, double* V);
+
 /* Host-only greedy grouping (no GPU needed): positions pos (N*2, host),
  * boxes of side W, optional order (NULL = index order), max_group (0 =
  * unlimited).  Writes group_ptr (capacity N+1), group_pos (N), *n_groups.

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdint>
@@ -270,6 +271,8 @@ struct pty_handle {
   pty_rpie_params iter_params{};
   long long iter_launch[PTY_K_COUNT] = {0};
   long long iter_patches = 0;
+  double* modes_G = nullptr;  // Gram matrix of the probe modes (M*M complex double)
+  float2* modes_V = nullptr;  // their eigenvectors, as the mixing matrix
   float* err_slot = nullptr;  // the captured iteration's error
   bool graphs_off = false;    // capture failed once: launch directly
   // A host pattern stack whose upload pty_set_data_async deferred: the next
@@ -1365,6 +1368,56 @@ int pty_group_positions(const float* pos, int N, int W, int max_group, const int
   return PTY_OK;
 }
 
+int pty_hermitian_eig(int M, const double* A, double* w, double* V) {
+  g_err.clear();
+  if (!A || !w || !V) return fail(PTY_EINVAL, "null argument");
+  if (M < 1 || M > 16) return fail(PTY_EINVAL, "M=%d outside 1..16", M);
+  std::vector<std::complex<double>> a((size_t)M * M), v((size_t)M * M);
+  for (size_t i = 0; i < a.size(); ++i) {
+    if (!std::isfinite(A[2 * i]) || !std::isfinite(A[2 * i + 1]))
+      return fail(PTY_EDATA, "matrix entry %zu not finite", i);
+    a[i] = std::complex<double>(A[2 * i], A[2 * i + 1]);
+  }
+  if (pty::hermitian_eig(M, a.data(), w, v.data()) != 0) return fail(PTY_EINVAL, "eigensolver");
+  for (size_t i = 0; i < v.size(); ++i) {
+    V[2 * i] = v[i].real();
+    V[2 * i + 1] = v[i].imag();
+  }
+  return PTY_OK;
+}
+
+int pty_orthogonalize_probe(pty_handle* h, double* power_out) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  if (!h->has_data) return fail(PTY_ESTATE, "pty_set_data has not been called");
+  const int M = h->M, WW = h->W * h->W;
+  if (!h->modes_G) TRY(alloc_into(h, h->modes_G, (size_t)2 * M * M));  // double2 as 2 doubles
+  if (!h->modes_V) TRY(alloc_into(h, h->modes_V, (size_t)M * M));
+  CU(pty::launch_gram(h->P, M, WW, h->modes_G, h->stream));
+  std::vector<double> g((size_t)2 * M * M);
+  CU(cudaMemcpyAsync(g.data(), h->modes_G, sizeof(double) * g.size(), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  std::vector<std::complex<double>> G((size_t)M * M), V((size_t)M * M);
+  for (size_t i = 0; i < G.size(); ++i) {
+    if (!std::isfinite(g[2 * i]) || !std::isfinite(g[2 * i + 1]))
+      return fail(PTY_EDATA, "probe holds a non-finite value");
+    G[i] = std::complex<double>(g[2 * i], g[2 * i + 1]);
+  }
+  std::vector<double> w(M);
+  if (pty::hermitian_eig(M, G.data(), w.data(), V.data()) != 0)
+    return fail(PTY_EINVAL, "eigensolver");
+  std::vector<float2> vf((size_t)M * M);
+  for (size_t i = 0; i < vf.size(); ++i)
+    vf[i] = make_float2((float)V[i].real(), (float)V[i].imag());
+  CU(cudaMemcpyAsync(h->modes_V, vf.data(), sizeof(float2) * vf.size(), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(pty::launch_mix(h->P, M, WW, h->modes_V, h->stream));
+  CU(pty::launch_pmax(h->tl, h->P, h->pmax_part, h->stream));
+  CU(cudaStreamSynchronize(h->stream));  // vf is host memory of this call
+  if (power_out) std::copy(w.begin(), w.end(), power_out);
+  return PTY_OK;
+}
 
 // ===================================================================== batch
 struct pty_batch {

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <complex>
+
 namespace pty {
 
 struct UpdArgs {
@@ -94,6 +96,14 @@ cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
                                cudaStream_t s);
 cudaError_t launch_pmax(const Tiling& t, const float2* P, float* pmax_part,
                         cudaStream_t s);
+// Probe-mode orthogonalisation (pty_modes.cu): Gram matrix (M*M double2,
+// row k column l = sum_r conj(P_k) P_l), the host Hermitian eigensolver
+// (decreasing eigenvalues; 0 on success) and the in-place mixing
+// P'_m = sum_k V[k][m] P_k.
+cudaError_t launch_gram(const float2* P, int M, int WW, void* G, cudaStream_t s);
+int hermitian_eig(int M, const std::complex<double>* A, double* w, std::complex<double>* V);
+cudaError_t launch_mix(float2* P, int M, int WW, const float2* V, cudaStream_t s);
+
 // Error normalised by 1/sum(I): inv_sumI, or the device sum when sum_dev != NULL.
 cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
                               const unsigned long long* sum_dev, float* out, cudaStream_t s);

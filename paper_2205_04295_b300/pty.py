@@ -85,6 +85,8 @@ _SIGS = {
     "pty_destroy": (c_int, [c_void_p]),
     "pty_set_data": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "pty_set_data_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "pty_orthogonalize_probe": (c_int, [c_void_p, c_void_p]),
+    "pty_hermitian_eig": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
     "pty_set_scan_order": (c_int, [c_void_p, c_void_p]),
     "pty_run_iterations": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams), c_void_p]),
     "pty_refine_positions": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams),
@@ -190,6 +192,17 @@ def group_positions(pos, W, max_group=0, order=None):
                                     None if od is None else od.ctypes.data,
                                     gptr.ctypes.data, gpos.ctypes.data, ctypes.byref(ng)))
     return [gpos[gptr[g]:gptr[g + 1]].copy() for g in range(ng.value)]
+
+
+def hermitian_eig(A):
+    """Eigenvalues (decreasing) and eigenvectors (columns, largest entry of
+    each real positive) of a Hermitian matrix, by the library's host solver."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    M = A.shape[0]
+    w = np.zeros(M, np.float64)
+    V = np.zeros((M, M), np.complex128)
+    check(lib().pty_hermitian_eig(M, A.ctypes.data, w.ctypes.data, V.ctypes.data))
+    return w, V
 
 
 def fft2_(x, inverse=False):
@@ -357,6 +370,13 @@ class Problem:
         check(lib().pty_loss_grad(self.h, O.data_ptr(), P.data_ptr(), pos.data_ptr(), float(delta),
                                   out.data_ptr(), gO.data_ptr(), gP.data_ptr(), gpos.data_ptr()))
         return out, gO, gP, gpos
+
+    def orthogonalize_probe(self):
+        """Orthogonalise the probe modes in place; returns their powers
+        (decreasing)."""
+        w = np.zeros(self.M, np.float64)
+        check(lib().pty_orthogonalize_probe(self.h, w.ctypes.data))
+        return w
 
     def set_tiling(self, R=0, ppc=0, CB=0, scratch_bytes=0, ppcb=0):
         check(lib().pty_set_tiling(self.h, ctypes.byref(Tiling(R, ppc, CB, scratch_bytes, ppcb))))
