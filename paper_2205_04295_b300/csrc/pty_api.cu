@@ -685,9 +685,10 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
     return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
   if (cudaError_t e = pty::set_grad_smem(h->tl); e != cudaSuccess)
     return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
-  if (h->tlr.smA > 227 * 1024 || h->tlr.smB > 227 * 1024 || h->tlr.smC > 227 * 1024 ||
-      h->tl.smC > 227 * 1024)
-    return bail(fail(PTY_EINVAL, "W=%d with M=%d modes exceeds shared memory", h->W, h->M));
+  if (!pty::tiling_fits(h->tl) || !pty::tiling_fits(h->tlr))
+    return bail(fail(PTY_EINVAL,
+                     "W=%d with M=%d modes exceeds the per-CTA thread or shared-memory limits",
+                     h->W, h->M));
   const size_t W2 = (size_t)h->W * h->W;
   const size_t budget = d->scratch_bytes ? d->scratch_bytes : ((size_t)64 << 20);
   h->Qc = (int)std::max<size_t>(1, budget / (W2 * h->tl.npl * sizeof(float2)));
@@ -1239,8 +1240,7 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   if (t->ppcb < 0 || t->ppcb > 64) return fail(PTY_EINVAL, "column patches per CTA %d", t->ppcb);
   pty::Tiling nt = pty::make_tiling(W, M, false, 512, t->R, t->ppc, t->CB);
   if (t->ppcb > 0) nt.ppcb = t->ppcb;
-  if (nt.smA > 227 * 1024 || nt.smB > 227 * 1024 || nt.smC > 227 * 1024)
-    return fail(PTY_EINVAL, "tiling needs too much shared memory");
+  if (!pty::tiling_fits(nt)) return fail(PTY_EINVAL, "tiling exceeds the per-CTA limits");
   // the registration passes take the same geometry where it fits their extra
   // crop plane, and the same patches per chunk
   // (the extra plane can push the column pass past two CTAs per SM: halve
@@ -1252,9 +1252,7 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
     nr = pty::make_tiling(W, M, true, 512, t->R, t->ppc, cbr);
   }
   if (t->ppcb > 0) nr.ppcb = t->ppcb;
-  if ((t->R && (M + 1) * t->R * L > 256) ||
-      nr.smA > 227 * 1024 || nr.smB > 227 * 1024 || nr.smC > 227 * 1024)
-    nr = h->tlr;
+  if (!pty::tiling_fits(nr)) nr = h->tlr;
   const size_t W2 = (size_t)W * W;
   const size_t budget = t->scratch_bytes ? t->scratch_bytes : ((size_t)64 << 20);
   const int Qc = (int)std::min<size_t>((size_t)h->N, std::max<size_t>(1, budget / (W2 * M * sizeof(float2))));
@@ -1532,6 +1530,9 @@ int pty_batch_run(pty_batch* b, int n_iter, const pty_rpie_params* p) {
     TRY(regroup(h, p->max_group));
     TRY(ensure_err_cap(h, n_iter));
     const pty::Tiling t = pty::make_tiling(h->W, h->M, false, 256);
+    if (t.thrA > 256 || t.thrB > 256 || t.thrC > 256)
+      return fail(PTY_EINVAL, "problem %d: W=%d with M=%d modes exceeds the batched CTA", i,
+                  h->W, h->M);
     smem = std::max(smem, pty::batch_smem(t));
     pty::BatchProb& pb = probs[i];
     pb.W = h->W; pb.M = h->M; pb.N = h->N; pb.Hx = h->Hx;

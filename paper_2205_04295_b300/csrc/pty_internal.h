@@ -29,6 +29,9 @@ struct Tiling {
 };
 
 bool supported_W(int W);
+// The pass kernels' launch bounds (rows 256, columns 384 threads) and the
+// opt-in shared memory hold for this tiling.
+bool tiling_fits(const Tiling& t);
 
 // Largest dynamic shared memory a block may opt in to on the current device.
 // Every kernel's opt-in limit is set to this value: the attribute is global

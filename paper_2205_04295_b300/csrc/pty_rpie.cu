@@ -273,6 +273,12 @@ int lanes_per_line(int W) {
   return L;
 }
 
+bool tiling_fits(const Tiling& t) {
+  const size_t lim = (size_t)smem_optin() - 1024;
+  return t.thrA <= 256 && t.thrB <= 384 && t.thrC <= 256 && t.smA <= lim && t.smB <= lim &&
+         t.smC <= lim;
+}
+
 bool supported_W(int W) {
   return W == 32 || W == 64 || W == 96 || W == 128 || W == 192 || W == 256;
 }

@@ -82,8 +82,12 @@ def make_probe(W, M, photons, occupancy):
     r2 = (x * x + y * y) / (R * R)
     base = (r2 <= 1.0) * np.exp(1j * 4.0 * np.pi * r2)
     shapes = [np.ones_like(x), x / R, y / R, x * y / R ** 2, (x * x - y * y) / R ** 2]
+    # further modes (up to 16): more monomials x^a y^b / R^(a+b), by degree
+    for a_, b_ in ((2, 0), (2, 1), (1, 2), (3, 0), (0, 3), (2, 2), (3, 1), (1, 3), (4, 0),
+                   (0, 4), (3, 2)):
+        shapes.append(x ** a_ * y ** b_ / R ** (a_ + b_))
     if M > len(shapes):
-        raise ValueError("at most 5 probe modes are generated")
+        raise ValueError("at most %d probe modes are generated" % len(shapes))
     modes = []
     for k in range(M):
         v = base * shapes[k]

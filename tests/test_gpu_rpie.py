@@ -228,6 +228,22 @@ def test_error_codes():
     assert e.value.code == pty.PTY_EINVAL
 
 
+def test_maximum_mode_count_keeps_parity_and_one_more_is_rejected():
+    """256^2 patterns take at most 12 modes (the column pass holds 2 columns x
+    16 lanes per mode in at most 384 threads); 12 keeps one-iteration parity,
+    13 is refused at init instead of failing at launch."""
+    from paper_2205_04295_b300 import pty
+    wl = synth.tiny(W=256, M=12, ny=2, nx=2, step=40.0, seed=91, photons=1e6)
+    d = build(wl)
+    check_one_iteration(wl, d)
+    with pytest.raises(pty.PtyError) as e:
+        pty.Problem(256, 13, 4, 400, 400)
+    assert e.value.code == pty.PTY_EINVAL
+    with pytest.raises(pty.PtyError) as e:
+        pty.Problem(64, 17, 4, 200, 200)
+    assert e.value.code == pty.PTY_EINVAL
+
+
 def test_device_inputs_equal_host_inputs():
     import torch
     wl = synth.tiny(W=64, M=2, ny=3, nx=3, step=10.0, seed=18)
