@@ -133,7 +133,7 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
 }
 
 // ---------------------------------------------------------------- pass B
-// Request (cp.async) the column block [c0, c0 + CB) of the MA mode planes of patch
+// Request (cp.async) the column block [c0, c0 + CB) of the MA planes of patch
 // slot lp into `stage` ([plane][row][column]) and the block's counts into
 // `cnt` ([row][column], rows and columns fftshifted, DC at the centre of the
 // stored pattern).  CB is even, so every segment is 16-byte aligned.
