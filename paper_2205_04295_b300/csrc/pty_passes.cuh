@@ -74,12 +74,16 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   float2* Prow = tw + W;
   float2* tbuf = Prow + M * R * W;
   float2* ost = tbuf + (M + xo) * R * G::LP;  // 2 x R x W crop rows
+  int2* scor = reinterpret_cast<int2*>(ost + 2 * R * W);  // ppc corners
   __shared__ float red[32];
 
   const int r0 = bx * R;
   const int nrb = W / R;
   const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
-  if (p0 < p1) rows_fwd_stage<W>(O, Hx, corners[ids[p0]], R, r0, ost);
+  // the CTA's corners, once: no dependent index loads inside the patch loop
+  for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) scor[t] = corners[ids[p0 + t]];
+  __syncthreads();
+  if (p0 < p1) rows_fwd_stage<W>(O, Hx, scor[0], R, r0, ost);
   cp_async_commit();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
@@ -97,7 +101,7 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
     cp_async_wait<0>();
     __syncthreads();  // this patch's crop rows have landed; lbuf is free
     if (lp + 1 < p1)
-      rows_fwd_stage<W>(O, Hx, corners[ids[lp + 1]], R, r0, ost + ((lp + 1 - p0) & 1) * R * W);
+      rows_fwd_stage<W>(O, Hx, scor[lp + 1 - p0], R, r0, ost + ((lp + 1 - p0) & 1) * R * W);
     cp_async_commit();
     float omax = 0.f;
     if (act && lane < G::N2) {
@@ -188,6 +192,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
   float2* tbuf = stage + (STAGE ? M * W * CB : 0);               // M x CB lines
   float* Sb = reinterpret_cast<float*>(tbuf + M * CB * G::LP);   // M x W x CB
   uint16_t* cnt = reinterpret_cast<uint16_t*>(Sb + M * CB * W);  // 2 x W x CB
+  int* sids = reinterpret_cast<int*>(cnt + 2 * W * CB);           // ppcb pattern ids
   __shared__ float red[32];
 
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
@@ -200,12 +205,14 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
   const float2* srow = stage + kk0 * W * CB + c;
   const int nw = (blockDim.x + 31) >> 5;
   const int p0 = by * ppcb, p1 = min(npatch, p0 + ppcb);
+  for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) sids[t] = ids[p0 + t];
+  __syncthreads();
   if constexpr (STAGE) {
-    if (p0 < p1) cols_stage<W, CB>(scratch, I, ids[p0], p0, npl, M, c0, stage, cnt);
+    if (p0 < p1) cols_stage<W, CB>(scratch, I, sids[0], p0, npl, M, c0, stage, cnt);
     cp_async_commit();
   }
   for (int lp = p0; lp < p1; ++lp) {
-    const int j = ids[lp];
+    const int j = sids[lp - p0];
     const uint16_t* cn = cnt + (STAGE ? ((lp - p0) & 1) * W * CB : 0);
     float2* col = scratch + ((size_t)lp * npl + kk0) * W * W + c0 + c;
     if constexpr (STAGE) {
@@ -219,7 +226,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
       }
       __syncthreads();  // the stage is free: request the next patch
       if (lp + 1 < p1)
-        cols_stage<W, CB>(scratch, I, ids[lp + 1], lp + 1, npl, M, c0, stage,
+        cols_stage<W, CB>(scratch, I, sids[lp + 1 - p0], lp + 1, npl, M, c0, stage,
                           cnt + ((lp + 1 - p0) & 1) * W * CB);
       cp_async_commit();
     } else {
@@ -339,7 +346,9 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   float2* zst = onew + (refine ? R * W : 0);  // M x R x W far-field rows
   float* invd = reinterpret_cast<float*>(zst + M * R * W);  // alpha_O / denominator
   float* den = invd + R * W;
-  __shared__ float s_pmax, s_omax;
+  int2* scor = reinterpret_cast<int2*>(den + R * W);         // ppc corners
+  float* som = reinterpret_cast<float*>(scor + ppc);         // ppc crop maxima
+  __shared__ float s_pmax;
 
   const int r0 = bx * R;
   const int nrb = W / R;
@@ -379,19 +388,25 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     }
   }
   const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
+  // the CTA's corners and crop maxima max_r |o_j|^2 (reduced over the row
+  // blocks of pass A), once: no dependent global loads inside the patch loop
+  {
+    const int nw = (blockDim.x + 31) >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) scor[t] = corners[ids[p0 + t]];
+    for (int t = w; t < p1 - p0; t += nw) {
+      float m = 0.f;
+      for (int i = l; i < nrb; i += 32) m = fmaxf(m, omax_part[(size_t)(p0 + t) * nrb + i]);
+      m = warp_max(m);
+      if (l == 0) som[t] = m;
+    }
+  }
+  __syncthreads();
   float osum_local = 0.f;
-  if (p0 < p1)
-    rows_inv_stage<W>(scratch, O, Hx, corners[ids[p0]], p0, npl, M, R, r0, zst, ostash);
+  if (p0 < p1) rows_inv_stage<W>(scratch, O, Hx, scor[0], p0, npl, M, R, r0, zst, ostash);
   cp_async_commit();
   for (int lp = p0; lp < p1; ++lp) {
-    const int2 cc = corners[ids[lp]];
+    const int2 cc = scor[lp - p0];
     const float2* oc = ostash + ((lp - p0) & 1) * R * W;
-    if (threadIdx.x < 32) {
-      float m = 0.f;
-      for (int i = threadIdx.x; i < nrb; i += 32) m = fmaxf(m, omax_part[(size_t)lp * nrb + i]);
-      m = warp_max(m);
-      if (threadIdx.x == 0) s_omax = m;
-    }
     cp_async_wait<0>();
     __syncthreads();  // this patch's rows have landed
     if (act && lane < G::N1) {
@@ -403,7 +418,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     }
     __syncthreads();  // the far-field stage is free: request the next patch
     if (lp + 1 < p1)
-      rows_inv_stage<W>(scratch, O, Hx, corners[ids[lp + 1]], lp + 1, npl, M, R, r0, zst,
+      rows_inv_stage<W>(scratch, O, Hx, scor[lp + 1 - p0], lp + 1, npl, M, R, r0, zst,
                         ostash + ((lp + 1 - p0) & 1) * R * W);
     cp_async_commit();
     float2 v[G::N1];
@@ -421,7 +436,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
       }
     }
     __syncthreads();
-    const float om = s_omax;
+    const float om = som[lp - p0];
     for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
       const int rr = e / W, c = e - rr * W;
       const float2 o = oc[e];

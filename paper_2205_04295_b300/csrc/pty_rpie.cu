@@ -338,15 +338,16 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   t.thrA = round32(MA * R * L);
   t.thrC = round32(M * R * L);
   t.thrB = round32(M * CB * L);
-  t.smA = (size_t)(W + M * R * W + MA * R * LP + 2 * R * W) * sizeof(float2);
+  t.smA = (size_t)(W + M * R * W + MA * R * LP + 2 * R * W + t.ppc) * sizeof(float2);
   // pass B transforms the M modes only (the crop plane's column DFTs are
   // taken by the registration's correlation pass)
   t.smB = (size_t)(W + M * W * CB + M * CB * LP) * sizeof(float2) +
-          (size_t)M * CB * W * sizeof(float) + (size_t)2 * W * CB * sizeof(uint16_t);
+          (size_t)M * CB * W * sizeof(float) + (size_t)2 * W * CB * sizeof(uint16_t) +
+          (size_t)64 * sizeof(int);  // pattern ids of up to 64 patches per CTA
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
   t.smC = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + M * R * W) * sizeof(float2) +
-          (size_t)2 * R * W * sizeof(float);
+          (size_t)2 * R * W * sizeof(float) + (size_t)t.ppc * (sizeof(int2) + sizeof(float));
   t.n_pmax = std::max(1, std::min(1024, W * W / 256));
   return t;
 }
