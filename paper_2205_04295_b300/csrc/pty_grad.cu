@@ -109,9 +109,13 @@ k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__
   float2* tbuf = Prow + M * R * W;
   float2* obuf = tbuf + M * R * G::LP;  // R x W interpolated crop rows
   float2* st = obuf + R * W;            // 2 x (R + 1) x (W + 1) object rows
+  Bil* sb = reinterpret_cast<Bil*>(st + 2 * (R + 1) * SP);  // ppc crop geometries
   const int r0 = blockIdx.x * R;
   const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
-  if (p0 < p1) grad_stage<W>(O, Hx, bil_of(pos, ids[p0]), R, r0, st);
+  // the CTA's crop geometries, once: no dependent loads inside the patch loop
+  for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) sb[t] = bil_of(pos, ids[p0 + t]);
+  __syncthreads();
+  if (p0 < p1) grad_stage<W>(O, Hx, sb[0], R, r0, st);
   cp_async_commit();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
@@ -123,13 +127,12 @@ k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
   for (int lp = p0; lp < p1; ++lp) {
-    const Bil b = bil_of(pos, ids[lp]);
+    const Bil b = sb[lp - p0];
     const float2* sc = st + ((lp - p0) & 1) * (R + 1) * SP;
     cp_async_wait<0>();
     __syncthreads();  // this patch's rows have landed; obuf and lbuf are free
     if (lp + 1 < p1)
-      grad_stage<W>(O, Hx, bil_of(pos, ids[lp + 1]), R, r0,
-                    st + ((lp + 1 - p0) & 1) * (R + 1) * SP);
+      grad_stage<W>(O, Hx, sb[lp + 1 - p0], R, r0, st + ((lp + 1 - p0) & 1) * (R + 1) * SP);
     cp_async_commit();
     for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
       const int rr = e / W, c = e - rr * W;
@@ -177,10 +180,17 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
   float2* gp = tbuf + TB;           // dL/dP partial sums of this CTA
   float2* obuf = gp + M * R * W;    // R x W interpolated crop rows
   float2* st = obuf + R * W;        // 2 x (R + 1) x (W + 1) object rows
+  Bil* sb = reinterpret_cast<Bil*>(st + 2 * (R + 1) * SP);  // ppc crop geometries
+  int* sj = reinterpret_cast<int*>(sb + ppc);                // ppc pattern ids
   __shared__ float red2[64];
   const int r0 = blockIdx.x * R, nrb = W / R;
   const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
-  auto stage = [&](int q, float2* stq) { grad_stage<W>(O, Hx, bil_of(pos, ids[q]), R, r0, stq); };
+  for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) {
+    sj[t] = ids[p0 + t];
+    sb[t] = bil_of(pos, sj[t]);
+  }
+  __syncthreads();
+  auto stage = [&](int q, float2* stq) { grad_stage<W>(O, Hx, sb[q - p0], R, r0, stq); };
   if (p0 < p1) stage(p0, st);
   cp_async_commit();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
@@ -194,8 +204,8 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
   for (int lp = p0; lp < p1; ++lp) {
-    const int j = ids[lp];
-    const Bil b = bil_of(pos, j);
+    const int j = sj[lp - p0];
+    const Bil b = sb[lp - p0];
     const float2* sc = st + ((lp - p0) & 1) * (R + 1) * SP;
     cp_async_wait<0>();
     __syncthreads();  // this patch's rows have landed
@@ -346,7 +356,8 @@ static size_t grad_inv_smem(const Tiling& t) {
   }
   const int TB = std::max(t.M * t.R * LP, t.M * t.R * t.W);
   return (size_t)(t.W + t.M * t.R * t.W + TB + t.M * t.R * t.W + t.R * t.W +
-                  2 * (t.R + 1) * (t.W + 1)) * sizeof(float2);
+                  2 * (t.R + 1) * (t.W + 1)) * sizeof(float2) +
+         (size_t)t.ppc * (sizeof(Bil) + sizeof(int));
 }
 
 static size_t grad_fwd_smem(const Tiling& t) {
@@ -360,7 +371,7 @@ static size_t grad_fwd_smem(const Tiling& t) {
     default: LP = Line<256>::LP; break;
   }
   return (size_t)(t.W + t.M * t.R * t.W + t.M * t.R * LP + t.R * t.W +
-                  2 * (t.R + 1) * (t.W + 1)) * sizeof(float2);
+                  2 * (t.R + 1) * (t.W + 1)) * sizeof(float2) + (size_t)t.ppc * sizeof(Bil);
 }
 
 cudaError_t set_grad_smem(const Tiling& t) {
