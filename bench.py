@@ -65,7 +65,7 @@ def per_pass_flops(W, M):
 # `bench.py --workload spiral_256_n2000` (256^2 x 5 modes, launches of ~13.5
 # patches).  Valid for the pass kernels as profiled; a launch's traffic is
 # this times its patches.
-DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.353e6, "cols": 0.399e6, "rows_inv": 0.281e6}}
+DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.360e6, "cols": 0.443e6, "rows_inv": 0.251e6}}
 
 
 def fp32_peak_tflops():
