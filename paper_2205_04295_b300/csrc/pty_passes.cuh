@@ -27,6 +27,13 @@ namespace pty {
 
 namespace {
 
+// Programmatic dependent launch: the kernels of a group's chain let the next
+// kernel start its independent prologue while they drain, and wait for the
+// previous kernel (its completion and memory) before touching its results.
+// Both are no-ops in a launch without the programmatic attribute.
+PTY_D void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+PTY_D void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 
 PTY_D float warp_sum(float v) {
 #pragma unroll
@@ -80,12 +87,14 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   const int r0 = bx * R;
   const int nrb = W / R;
   const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
+  pdl_trigger();
   // the CTA's corners, once: no dependent index loads inside the patch loop
   for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) scor[t] = corners[ids[p0 + t]];
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  pdl_wait();  // O, P and the partial maxima belong to the previous kernels
   __syncthreads();
   if (p0 < p1) rows_fwd_stage<W>(O, Hx, scor[0], R, r0, ost);
   cp_async_commit();
-  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
     Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
@@ -205,7 +214,9 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
   const float2* srow = stage + kk0 * W * CB + c;
   const int nw = (blockDim.x + 31) >> 5;
   const int p0 = by * ppcb, p1 = min(npatch, p0 + ppcb);
+  pdl_trigger();
   for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) sids[t] = ids[p0 + t];
+  pdl_wait();  // the far field comes from pass A
   __syncthreads();
   if constexpr (STAGE) {
     if (p0 < p1) cols_stage<W, CB>(scratch, I, sids[0], p0, npl, M, c0, stage, cnt);
@@ -352,7 +363,9 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
 
   const int r0 = bx * R;
   const int nrb = W / R;
+  pdl_trigger();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  pdl_wait();  // everything below is written by earlier kernels
   if (threadIdx.x < 32) {
     float m = 0.f;
     for (int i = threadIdx.x; i < n_pmax; i += 32) m = fmaxf(m, pmax_part[i]);
@@ -493,6 +506,8 @@ PTY_D void probe_apply_body(float2* P, int M, int WW, const float2* pnum, const 
                             const float* osum, int nslots, float alpha_P, float reg_eps,
                             float* pmax_part, int bx, int gx) {
   __shared__ float red[32];
+  pdl_trigger();
+  pdl_wait();
   float os = 0.f;
   for (int s = 0; s < nslots; ++s) os += osum[s];
   const float guard = reg_eps * os;

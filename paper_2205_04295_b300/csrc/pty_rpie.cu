@@ -283,6 +283,23 @@ bool supported_W(int W) {
   return W == 32 || W == 64 || W == 96 || W == 128 || W == 192 || W == 256;
 }
 
+// Launch with programmatic stream serialisation (see pdl_trigger/pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 #define PTY_DISPATCH_W(W, ...)                               \
   switch (W) {                                               \
     case 32: { constexpr int WW = 32; __VA_ARGS__; } break;   \
@@ -384,10 +401,11 @@ cudaError_t launch_rows_fwd(const Tiling& t, const float2* O, int Hx, const floa
                             cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
-  PTY_DISPATCH_W(t.W, (k_rows_fwd<WW><<<grid, t.thrA, t.smA, s>>>(O, Hx, P,
-                                    t.M, t.R, t.ppc, ids, corners, npatch, tw, scratch,
-                                    omax_part, t.npl, t.xo)));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(t.W, e = launch_pdl(k_rows_fwd<WW>, grid, dim3(t.thrA), t.smA, s, O, Hx, P,
+                                     t.M, t.R, t.ppc, ids, corners, npatch, tw, scratch,
+                                     omax_part, t.npl, t.xo));
+  return e;
 }
 
 // Pass A with the plain layout (M planes, no crop plane) whatever t says:
@@ -409,10 +427,12 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         float eps, float* err_part, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
-  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, (k_cols<WW, CBB, false><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, I, ids, tw, inv_w, eps, err_part, t.npl, t.ppcb,
-                          npatch))));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = launch_pdl(k_cols<WW, CBB, false>, grid,
+                                                           dim3(t.thrB), t.smB, s, scratch, t.M,
+                                                           I, ids, tw, inv_w, eps, err_part,
+                                                           t.npl, t.ppcb, npatch)));
+  return e;
 }
 
 cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I,
@@ -434,20 +454,20 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             float* osum, int accumulate, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
-  PTY_DISPATCH_W(t.W, (k_rows_inv<WW><<<grid, t.thrC, t.smC, s>>>(O, Hx, P,
-                                    t.M, t.R, t.ppc, ids, corners, npatch, scratch, omax_part,
-                                    pmax_part, t.n_pmax, tw, a, pnum, pden, osum, accumulate,
-                                    t.npl, t.refine)));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(t.W, e = launch_pdl(k_rows_inv<WW>, grid, dim3(t.thrC), t.smC, s, O, Hx, P,
+                                     t.M, t.R, t.ppc, ids, corners, npatch, scratch, omax_part,
+                                     pmax_part, t.n_pmax, tw, a, pnum, pden, osum, accumulate,
+                                     t.npl, t.refine));
+  return e;
 }
 
 cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
                                const float* pden, const float* osum, int nslots,
                                float alpha_P, float reg_eps, float* pmax_part,
                                cudaStream_t s) {
-  k_probe_apply<<<t.n_pmax, 256, 0, s>>>(P, t.M, t.W * t.W, pnum, pden, osum, nslots,
-                                         alpha_P, reg_eps, pmax_part);
-  return cudaGetLastError();
+  return launch_pdl(k_probe_apply, dim3(t.n_pmax), dim3(256), 0, s, P, t.M, t.W * t.W, pnum,
+                    pden, osum, nslots, alpha_P, reg_eps, pmax_part);
 }
 
 cudaError_t launch_pmax(const Tiling& t, const float2* P, float* pmax_part, cudaStream_t s) {
