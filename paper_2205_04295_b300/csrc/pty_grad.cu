@@ -17,6 +17,7 @@
 #include "pty_copy.cuh"
 #include "pty_fft.cuh"
 #include "pty_internal.h"
+#include "pty_pdl.cuh"
 
 #include <algorithm>
 
@@ -112,12 +113,14 @@ k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__
   Bil* sb = reinterpret_cast<Bil*>(st + 2 * (R + 1) * SP);  // ppc crop geometries
   const int r0 = blockIdx.x * R;
   const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  pdl_trigger();
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  pdl_wait();  // positions, object and probe may come from the previous kernel
   // the CTA's crop geometries, once: no dependent loads inside the patch loop
   for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) sb[t] = bil_of(pos, ids[p0 + t]);
   __syncthreads();
   if (p0 < p1) grad_stage<W>(O, Hx, sb[0], R, r0, st);
   cp_async_commit();
-  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
     Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
@@ -185,6 +188,8 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
   __shared__ float red2[64];
   const int r0 = blockIdx.x * R, nrb = W / R;
   const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
+  pdl_trigger();
+  pdl_wait();  // the far field comes from the column pass
   for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) {
     sj[t] = ids[p0 + t];
     sb[t] = bil_of(pos, sj[t]);
@@ -274,6 +279,8 @@ k_grad_scatter(float2* __restrict__ gO, int Hx, const int* __restrict__ ids,
                const float* __restrict__ pos, const float2* __restrict__ scratch, int npl,
                int M) {
   const int lp = blockIdx.y;
+  pdl_trigger();
+  pdl_wait();  // G_o comes from the inverse-row pass
   const Bil b = bil_of(pos, ids[lp]);
   const float2* G = scratch + ((size_t)lp * npl + M) * W * W;
   const float w[2][2] = {{(1.f - b.fy) * (1.f - b.fx), (1.f - b.fy) * b.fx},
@@ -389,9 +396,11 @@ cudaError_t launch_grad_rows_fwd(const Tiling& t, const float2* O, int Hx, const
                                  const float2* tw, float2* scratch, int npl, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
-  PTY_DISPATCH_W(t.W, (k_grad_rows_fwd<WW><<<grid, t.thrC, grad_fwd_smem(t), s>>>(
-                          O, Hx, P, t.M, t.R, t.ppc, ids, pos, npatch, tw, scratch, npl)));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(t.W, e = launch_pdl(k_grad_rows_fwd<WW>, grid, dim3(t.thrC), grad_fwd_smem(t),
+                                     s, O, Hx, P, t.M, t.R, t.ppc, ids, pos, npatch, tw,
+                                     scratch, npl));
+  return e;
 }
 
 cudaError_t launch_grad_rows_inv(const Tiling& t, const float2* O, int Hx, const float2* P,
@@ -400,10 +409,11 @@ cudaError_t launch_grad_rows_inv(const Tiling& t, const float2* O, int Hx, const
                                  int accumulate, float* gpos_part, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
-  PTY_DISPATCH_W(t.W, (k_grad_rows_inv<WW><<<grid, t.thrC, grad_inv_smem(t), s>>>(
-                          O, Hx, P, t.M, t.R, t.ppc, ids, pos, npatch, scratch, npl, tw,
-                          gP_part, accumulate, gpos_part)));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(t.W, e = launch_pdl(k_grad_rows_inv<WW>, grid, dim3(t.thrC), grad_inv_smem(t),
+                                     s, O, Hx, P, t.M, t.R, t.ppc, ids, pos, npatch, scratch,
+                                     npl, tw, gP_part, accumulate, gpos_part));
+  return e;
 }
 
 cudaError_t launch_grad_scatter(int W, int M, float2* gO, int Hx, const int* ids,
@@ -411,9 +421,10 @@ cudaError_t launch_grad_scatter(int W, int M, float2* gO, int Hx, const int* ids
                                 cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   const int blocks = ((W + 1) * (W + 1) + 255) / 256;
-  PTY_DISPATCH_W(W, (k_grad_scatter<WW><<<dim3(blocks, npatch), 256, 0, s>>>(
-                        gO, Hx, ids, pos, scratch, npl, M)));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(W, e = launch_pdl(k_grad_scatter<WW>, dim3(blocks, npatch), dim3(256), 0, s,
+                                   gO, Hx, ids, pos, scratch, npl, M));
+  return e;
 }
 
 cudaError_t launch_grad_finish(const Tiling& t, int nslots, const float2* gP_part, float2* gP,

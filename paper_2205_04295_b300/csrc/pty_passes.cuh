@@ -22,17 +22,11 @@
 #include "pty_copy.cuh"
 #include "pty_fft.cuh"
 #include "pty_internal.h"
+#include "pty_pdl.cuh"
 
 namespace pty {
 
 namespace {
-
-// Programmatic dependent launch: the kernels of a group's chain let the next
-// kernel start its independent prologue while they drain, and wait for the
-// previous kernel (its completion and memory) before touching its results.
-// Both are no-ops in a launch without the programmatic attribute.
-PTY_D void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-PTY_D void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 
 PTY_D float warp_sum(float v) {

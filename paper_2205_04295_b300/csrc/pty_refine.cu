@@ -24,6 +24,7 @@
 #include "pty_copy.cuh"
 #include "pty_fft.cuh"
 #include "pty_internal.h"
+#include "pty_pdl.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -79,7 +80,9 @@ k_xcorr_cols(float2* __restrict__ scratch, int npl, int M, int CB,
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* tbuf = tw + W;
+  pdl_trigger();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  pdl_wait();  // both crops' row DFTs come from the passes
   const int lp = blockIdx.y, c0 = blockIdx.x * CB;
   const int c = threadIdx.x % CB, lane = threadIdx.x / CB;
   const bool act = lane < G::L;
@@ -138,7 +141,9 @@ k_xcorr_rows(const float2* __restrict__ scratch, int npl, int M, int RX,
   float2* tbuf = tw + W;
   __shared__ float rv[32];
   __shared__ int ri[32];
+  pdl_trigger();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  pdl_wait();  // X comes from the correlation column pass
   __syncthreads();
   const int lp = blockIdx.y, r0 = blockIdx.x * RX;
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
@@ -217,6 +222,8 @@ k_updft_part(const float2* __restrict__ scratch, int npl, int M, int nparts,
   __shared__ int ri[32];
   const int lp = blockIdx.y, u0 = blockIdx.x * RB;
   const float2* X = scratch + ((size_t)lp * npl + M) * W * W + (size_t)u0 * W;
+  pdl_trigger();
+  pdl_wait();  // X and the coarse peaks come from the correlation passes
   // all staging is asynchronous (cp.async): no thread waits on a load
   // before issuing the next one
   for (int e = threadIdx.x; e < RB * W; e += blockDim.x) {
@@ -291,6 +298,8 @@ k_updft_final(const int* __restrict__ ids, int W, int nblocks, int nparts,
               float* __restrict__ gap) {
   __shared__ float rv[32];
   __shared__ int ri[32];
+  pdl_trigger();
+  pdl_wait();  // the partial sums come from updft_part
   const int lp = blockIdx.x, j = ids[lp];
   int sy, sx;
   coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);
@@ -441,25 +450,27 @@ void make_up_roots(int W, int U, float2* out) {
 cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
                               const float2* tw, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
   PTY_DISPATCH_W(g.W, {
     using G = Line<WW>;
-    k_xcorr_cols<WW><<<dim3(WW / g.CBX, npatch), g.CBX * G::L, g.smX, s>>>(scratch, npl, M,
-                                                                           g.CBX, tw);
+    e = launch_pdl(k_xcorr_cols<WW>, dim3(WW / g.CBX, npatch), dim3(g.CBX * G::L), g.smX, s,
+                   scratch, npl, M, g.CBX, tw);
   });
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, int M,
                               int npatch, const float2* tw, float* cval, int* cidx,
                               cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
   PTY_DISPATCH_W(g.W, {
     using G = Line<WW>;
     const int thr = (g.RX * G::L + 31) / 32 * 32;
-    k_xcorr_rows<WW><<<dim3(WW / g.RX, npatch), thr, g.smR, s>>>(scratch, npl, M, g.RX, tw,
-                                                                 cval, cidx);
+    e = launch_pdl(k_xcorr_rows<WW>, dim3(WW / g.RX, npatch), dim3(thr), g.smR, s, scratch, npl,
+                   M, g.RX, tw, cval, cidx);
   });
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
@@ -472,11 +483,13 @@ cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const
     return cudaGetLastError();
   }
   const int nblocks = g.W / g.RB;
-  PTY_DISPATCH_W(g.W, (k_updft_part<WW><<<dim3(nblocks, npatch), 512, g.smU, s>>>(
-                          scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K, g.RB, part)));
-  k_updft_final<<<npatch, 256, 0, s>>>(ids, g.W, nblocks, nparts, cval, cidx, g.U, g.K, part,
-                                       shift, gap);
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(g.W, e = launch_pdl(k_updft_part<WW>, dim3(nblocks, npatch), dim3(512), g.smU,
+                                     s, scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K,
+                                     g.RB, part));
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_updft_final, dim3(npatch), dim3(256), 0, s, ids, g.W, nblocks, nparts,
+                    cval, cidx, g.U, g.K, part, shift, gap);
 }
 
 cudaError_t launch_adam(float* pos, float* m, float* v, const float* g, int N, float lr,

@@ -283,23 +283,6 @@ bool supported_W(int W) {
   return W == 32 || W == 64 || W == 96 || W == 128 || W == 192 || W == 256;
 }
 
-// Launch with programmatic stream serialisation (see pdl_trigger/pdl_wait).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t s,
-                       Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = g;
-  cfg.blockDim = b;
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
-
 #define PTY_DISPATCH_W(W, ...)                               \
   switch (W) {                                               \
     case 32: { constexpr int WW = 32; __VA_ARGS__; } break;   \
@@ -440,10 +423,12 @@ cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I
                              float delta, float* loss_part, int npl, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
-  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, (k_cols<WW, CBB, true><<<grid, t.thrB, t.smB, s>>>(
-                          scratch, t.M, I, ids, tw, inv_w, delta, loss_part, npl, t.ppcb,
-                          npatch))));
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = launch_pdl(k_cols<WW, CBB, true>, grid,
+                                                           dim3(t.thrB), t.smB, s, scratch, t.M,
+                                                           I, ids, tw, inv_w, delta, loss_part,
+                                                           npl, t.ppcb, npatch)));
+  return e;
 }
 
 cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
