@@ -271,6 +271,12 @@ struct pty_handle {
   pty_rpie_params iter_params{};
   long long iter_launch[PTY_K_COUNT] = {0};
   long long iter_patches = 0;
+  // tensor maps of the scratch for the column pass's TMA staging (plain and
+  // registration tilings); *tma_err is set by a TMA wait that timed out
+  CUtensorMap tmap_b{}, tmap_br{};
+  bool tma_b = false, tma_br = false;
+  int* tma_err = nullptr;
+  size_t scratch_n = 0;  // complex elements allocated in the scratch
   double* modes_G = nullptr;  // Gram matrix of the probe modes (M*M complex double)
   float2* modes_V = nullptr;  // their eigenvectors, as the mixing matrix
   float* err_slot = nullptr;  // the captured iteration's error
@@ -454,7 +460,9 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, bool refine = fals
     {
       pty_handle::Mark m(h, PTY_K_COLS);
       CU(pty::launch_cols(tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps,
-                          h->err_part, h->stream));
+                          h->err_part,
+                          refine ? (h->tma_br ? &h->tmap_br : nullptr) : (h->tma_b ? &h->tmap_b : nullptr),
+                          h->tma_err, h->stream));
     }
     {
       pty_handle::Mark m(h, PTY_K_ROWS_INV);
@@ -496,6 +504,26 @@ int ensure_err_cap(pty_handle* h, int n) {
 }
 
 int finish_upload(pty_handle* h);
+
+// (Re)encode the scratch's tensor maps for the current tilings; a tiling the
+// TMA rules do not admit stages with cp.async instead.
+void remap_scratch(pty_handle* h) {
+  const size_t planes = h->scratch_n / ((size_t)h->W * h->W);
+  h->tma_b = pty::encode_far_field_map(h->scratch, h->W, planes, h->tl.CB, &h->tmap_b);
+  h->tma_br = pty::encode_far_field_map(h->scratch, h->W, planes, h->tlr.CB, &h->tmap_br);
+}
+
+// A TMA wait in the column pass that timed out (reported at synchronising calls).
+int check_tma_error(pty_handle* h) {
+  int f = 0;
+  CU(cudaMemcpyAsync(&f, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (f) {
+    CU(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
+    return fail(PTY_ETIMEOUT, "a TMA copy of the column pass did not complete in time");
+  }
+  return PTY_OK;
+}
 
 // need_data: the call reads the data, so a deferred upload is completed first.
 int check_handle(pty_handle* h, bool need_data) {
@@ -711,6 +739,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->P, (size_t)h->M * W2)) ||
       (rc = alloc_into(h, h->tw, (size_t)h->W)) ||
       (rc = alloc_into(h, h->scratch, scratch_elems)) ||
+      (rc = alloc_into(h, h->tma_err, (size_t)1)) ||
       (rc = alloc_into(h, h->cval, nparts)) ||
       (rc = alloc_into(h, h->cidx, nparts)) ||
       (rc = alloc_into(h, h->gap, (size_t)h->N)) ||
@@ -735,11 +764,14 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->flag, (size_t)4)) ||
       (rc = alloc_into(h, h->sum_d, (size_t)1)))
     return bail(rc);
+  h->scratch_n = scratch_elems;
+  remap_scratch(h);
   std::vector<float2> tw(h->W);
   pty::make_twiddles(h->W, tw.data());
   if (cudaMemcpyAsync(h->tw, tw.data(), sizeof(float2) * h->W, cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->err_part, 0, sizeof(float) * err_part_cap, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(PTY_ECUDA, "initial copies failed"));
@@ -887,7 +919,7 @@ int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, floa
   if (err_out) {
     CU(cudaMemcpyAsync(err_out, h->err_iter, sizeof(float) * n_iter, cudaMemcpyDeviceToHost,
                        h->stream));
-    CU(cudaStreamSynchronize(h->stream));
+    TRY(check_tma_error(h));
   }
   return PTY_OK;
 }
@@ -1021,7 +1053,8 @@ int grad_run(pty_handle* h, const void* Ov, const void* Pv, const float* pos, fl
       CU(pty::launch_grad_rows_fwd(h->tl, O, h->Hx, P, idc, pos, nc, h->tw, h->scratch, npl,
                                    h->stream));
       CU(pty::launch_cols_grad(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, delta,
-                               h->err_part, npl, h->stream));
+                               h->err_part, npl, h->tma_b ? &h->tmap_b : nullptr, h->tma_err,
+                               h->stream));
       h->n_launch[PTY_K_GRAD] += 1;
       if (adjoint) {
         CU(pty::launch_grad_rows_inv(h->tl, O, h->Hx, P, idc, pos, nc, h->scratch, npl, h->tw,
@@ -1101,7 +1134,7 @@ int pty_get_groups(pty_handle* h, int* n_groups, int32_t* group_ptr, int32_t* gr
     TRY(check_mem_kind(mem_kind));                                                  \
     if (!dst) return fail(PTY_EINVAL, "null destination");                          \
     CU(cudaMemcpyAsync(dst, h->FIELD, sizeof(T) * (COUNT), kind_out(mem_kind), h->stream)); \
-    if (mem_kind == PTY_MEM_HOST) CU(cudaStreamSynchronize(h->stream));             \
+    if (mem_kind == PTY_MEM_HOST) TRY(check_tma_error(h)); /* synchronises */       \
     return PTY_OK;                                                                  \
   }
 
@@ -1269,7 +1302,9 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   if (scratch > cur_scratch) {
     h->dfree(h->scratch);
     h->scratch = nullptr;
+    h->scratch_n = 0;
     TRY(alloc_into(h, h->scratch, scratch));
+    h->scratch_n = scratch;
   }
   if (Qcr > h->Qcr) {
     h->dfree(h->cval); h->dfree(h->cidx);
@@ -1296,6 +1331,7 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   TRY(alloc_into(h, h->omax_part, std::max(omax_need, (size_t)std::max(Qc, Qcr) * W)));
   h->tl = nt;
   h->tlr = nr;
+  remap_scratch(h);
   h->Qc = Qc;
   h->Qcr = Qcr;
   h->err_part_n = (size_t)h->N * (W / nt.CB);

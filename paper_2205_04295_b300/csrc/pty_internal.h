@@ -1,6 +1,7 @@
 // Internal declarations shared by the host API (pty_api.cu) and the kernel
 // launchers (pty_rpie.cu, pty_refine.cu, pty_grad.cu).  Not part of the ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -63,13 +64,22 @@ cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx,
                                   const float2* P, const int* ids, const int2* corners,
                                   int npatch, const float2* tw, float2* scratch,
                                   float* omax_part, cudaStream_t s);
+// tm (may be NULL): tensor map of the scratch for TMA staging (see
+// encode_far_field_map); a TMA wait that times out sets *err.
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
-                        float eps, float* err_part, cudaStream_t s);
+                        float eps, float* err_part, const CUtensorMap* tm, int* err,
+                        cudaStream_t s);
 // Fourier-domain step of the gradient (amplitude loss, delta-smoothed).
 cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I,
                              const int* ids, int npatch, const float2* tw, float inv_w,
-                             float delta, float* loss_part, int npl, cudaStream_t s);
+                             float delta, float* loss_part, int npl, const CUtensorMap* tm,
+                             int* err, cudaStream_t s);
+// Tensor map over `planes` W x W complex64 planes at `base`, box CB x W x 1
+// (the column pass's block of one plane).  False if the driver entry point
+// is missing or the arguments break the TMA rules (the caller then stages
+// with cp.async).
+bool encode_far_field_map(const void* base, int W, size_t planes, int CB, CUtensorMap* out);
 // ---- differentiable forward model and adjoint (pty_grad.cu) ---------------
 cudaError_t launch_grad_rows_fwd(const Tiling& t, const float2* O, int Hx, const float2* P,
                                  const int* ids, const float* pos, int npatch,

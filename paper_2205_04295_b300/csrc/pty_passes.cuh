@@ -144,16 +144,28 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
 // slot lp into `stage` ([plane][row][column]) and the block's counts into
 // `cnt` ([row][column], rows and columns fftshifted, DC at the centre of the
 // stored pattern).  CB is even, so every segment is 16-byte aligned.
+// With a tensor map `tm` (planes of W x W complex over the scratch, box
+// CB x W x 1), thread 0 requests the MA boxes by TMA, completing on `mbar`;
+// without one, every thread issues 16-byte cp.async copies.
 template <int W, int CB>
 PTY_D void cols_stage(const float2* scratch, const uint16_t* I, int j, int lp, int npl, int MA,
-                      int c0, float2* stage, uint16_t* cnt) {
-  const int cpr = CB / 2;  // 16-byte chunks per row segment
-  const int nch = MA * W * cpr;
-  for (int i = threadIdx.x; i < nch; i += blockDim.x) {
-    const int h = i % cpr, row = i / cpr;  // row = plane * W + u
-    const int k = row / W, u = row - k * W;
-    cp_async<16>(stage + row * CB + 2 * h,
-                 scratch + (((size_t)lp * npl + k) * W + u) * W + c0 + 2 * h);
+                      int c0, float2* stage, uint16_t* cnt, const void* tm,
+                      unsigned long long* mbar) {
+  if (tm) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async();  // the stage was just read through the generic proxy
+      mbar_expect_tx(mbar, (unsigned)(MA * W * CB * sizeof(float2)));
+      for (int k = 0; k < MA; ++k) tma_load_3d(stage + k * W * CB, tm, c0, 0, lp * npl + k, mbar);
+    }
+  } else {
+    const int cpr = CB / 2;  // 16-byte chunks per row segment
+    const int nch = MA * W * cpr;
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) {
+      const int h = i % cpr, row = i / cpr;  // row = plane * W + u
+      const int k = row / W, u = row - k * W;
+      cp_async<16>(stage + row * CB + 2 * h,
+                   scratch + (((size_t)lp * npl + k) * W + u) * W + c0 + 2 * h);
+    }
   }
   // CB consecutive counts per detector row; CB divides W/2, so the block of
   // shifted columns does not wrap
@@ -187,11 +199,16 @@ template <int W, int CB, bool GRAD, bool STAGE = true>
 PTY_D void cols_body(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part, int npl, int ppcb, int npatch, int bx, int by) {
+       float* __restrict__ err_part, int npl, int ppcb, int npatch, int bx, int by,
+       const void* tm = nullptr, int* err = nullptr) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
+  __shared__ __align__(8) unsigned long long mbar;
   float2* tw = reinterpret_cast<float2*>(smem4);
-  float2* stage = tw + W;                                        // M x W x CB
+  // M x W x CB, 128-byte aligned (TMA destination; every plane's slice
+  // W * CB * 8 bytes is a multiple of 128)
+  float2* stage = reinterpret_cast<float2*>(
+      (reinterpret_cast<uintptr_t>(tw + W) + 127) & ~static_cast<uintptr_t>(127));
   float2* tbuf = stage + (STAGE ? M * W * CB : 0);               // M x CB lines
   float* Sb = reinterpret_cast<float*>(tbuf + M * CB * G::LP);   // M x W x CB
   uint16_t* cnt = reinterpret_cast<uint16_t*>(Sb + M * CB * W);  // 2 x W x CB
@@ -208,12 +225,15 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
   const float2* srow = stage + kk0 * W * CB + c;
   const int nw = (blockDim.x + 31) >> 5;
   const int p0 = by * ppcb, p1 = min(npatch, p0 + ppcb);
+  const bool tma = STAGE && tm != nullptr;
+  unsigned phase = 0;
   pdl_trigger();
   for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) sids[t] = ids[p0 + t];
+  if (tma && threadIdx.x == 0) mbar_init(&mbar, 1);
   pdl_wait();  // the far field comes from pass A
   __syncthreads();
   if constexpr (STAGE) {
-    if (p0 < p1) cols_stage<W, CB>(scratch, I, sids[0], p0, npl, M, c0, stage, cnt);
+    if (p0 < p1) cols_stage<W, CB>(scratch, I, sids[0], p0, npl, M, c0, stage, cnt, tm, &mbar);
     cp_async_commit();
   }
   for (int lp = p0; lp < p1; ++lp) {
@@ -221,8 +241,21 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
     const uint16_t* cn = cnt + (STAGE ? ((lp - p0) & 1) * W * CB : 0);
     float2* col = scratch + ((size_t)lp * npl + kk0) * W * W + c0 + c;
     if constexpr (STAGE) {
+      bool ok = true;
+      if (tma) {
+        ok = mbar_wait_bounded(&mbar, phase, 200000000ull);  // 0.2 s of the global timer
+        phase ^= 1;
+      }
       cp_async_wait<0>();
-      __syncthreads();  // this patch's block has landed
+      if (tma) {
+        if (__syncthreads_or(!ok)) {  // uniform: every thread leaves, none waits at a barrier
+          if (threadIdx.x == 0 && err) atomicExch(err, 1);
+          if (!ok) mbar_wait_bounded(&mbar, phase ^ 1, 200000000ull);  // the copy in flight
+          return;
+        }
+      } else {
+        __syncthreads();  // this patch's block has landed
+      }
       if (act && lane < G::N2) {
         float2 v[G::N1];
 #pragma unroll
@@ -232,7 +265,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
       __syncthreads();  // the stage is free: request the next patch
       if (lp + 1 < p1)
         cols_stage<W, CB>(scratch, I, sids[lp + 1 - p0], lp + 1, npl, M, c0, stage,
-                          cnt + ((lp + 1 - p0) & 1) * W * CB);
+                          cnt + ((lp + 1 - p0) & 1) * W * CB, tm, &mbar);
       cp_async_commit();
     } else {
       // the counts and the columns are requested together: one round trip

@@ -4,8 +4,11 @@
 // launchers (bodies in pty_passes.cuh).
 #include "pty_passes.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 namespace pty {
 
@@ -21,15 +24,17 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
   rows_fwd_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, tw_g, scratch, omax_part, npl, xo, blockIdx.x, blockIdx.y);
 }
 
-// 384 threads, two CTAs per SM: at most 80 registers a thread.
+// 384 threads, two CTAs per SM: at most 80 registers a thread.  With use_tma
+// the far-field block is staged by TMA through `tmap` (a time-out sets *err).
 template <int W, int CB, bool GRAD>
 __global__ void __launch_bounds__(384, 2)
 k_cols(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
-       float* __restrict__ err_part, int npl, int ppcb, int npatch) {
+       float* __restrict__ err_part, int npl, int ppcb, int npatch,
+       const __grid_constant__ CUtensorMap tmap, int use_tma, int* err) {
   cols_body<W, CB, GRAD>(scratch, M, I, ids, tw_g, inv_w, eps, err_part, npl, ppcb, npatch,
-                         blockIdx.x, blockIdx.y);
+                         blockIdx.x, blockIdx.y, use_tma ? &tmap : nullptr, err);
 }
 
 template <int W>
@@ -273,6 +278,33 @@ int lanes_per_line(int W) {
   return L;
 }
 
+bool encode_far_field_map(const void* base, int W, size_t planes, int CB, CUtensorMap* out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // TMA rules: 16-byte aligned base, strides multiples of 16 bytes, box inner
+  // extent (CB complex = 8 CB bytes) a multiple of 16, every box extent <= 256
+  if (!base || reinterpret_cast<uintptr_t>(base) % 16 || CB < 2 || CB % 2 || CB > 256 ||
+      W > 256 || planes < 1 || planes > (1ull << 32))
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)W, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)W * sizeof(float2), (cuuint64_t)W * W * sizeof(float2)};
+  const cuuint32_t box[3] = {(cuuint32_t)CB, (cuuint32_t)W, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return encode(out, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides,
+                box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool tiling_fits(const Tiling& t) {
   const size_t lim = (size_t)smem_optin() - 1024;
   return t.thrA <= 256 && t.thrB <= 384 && t.thrC <= 256 && t.smA <= lim && t.smB <= lim &&
@@ -343,7 +375,8 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   // taken by the registration's correlation pass)
   t.smB = (size_t)(W + M * W * CB + M * CB * LP) * sizeof(float2) +
           (size_t)M * CB * W * sizeof(float) + (size_t)2 * W * CB * sizeof(uint16_t) +
-          (size_t)64 * sizeof(int);  // pattern ids of up to 64 patches per CTA
+          (size_t)64 * sizeof(int) +  // pattern ids of up to 64 patches per CTA
+          128;                        // alignment of the stage
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
   t.smC = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + M * R * W) * sizeof(float2) +
@@ -407,27 +440,33 @@ cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx, cons
 
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
-                        float eps, float* err_part, cudaStream_t s) {
+                        float eps, float* err_part, const CUtensorMap* tm, int* err,
+                        cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   cudaError_t e = cudaSuccess;
+  CUtensorMap none{};
   PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = launch_pdl(k_cols<WW, CBB, false>, grid,
                                                            dim3(t.thrB), t.smB, s, scratch, t.M,
                                                            I, ids, tw, inv_w, eps, err_part,
-                                                           t.npl, t.ppcb, npatch)));
+                                                           t.npl, t.ppcb, npatch,
+                                                           tm ? *tm : none, tm ? 1 : 0, err)));
   return e;
 }
 
 cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I,
                              const int* ids, int npatch, const float2* tw, float inv_w,
-                             float delta, float* loss_part, int npl, cudaStream_t s) {
+                             float delta, float* loss_part, int npl, const CUtensorMap* tm,
+                             int* err, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   cudaError_t e = cudaSuccess;
+  CUtensorMap none{};
   PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = launch_pdl(k_cols<WW, CBB, true>, grid,
                                                            dim3(t.thrB), t.smB, s, scratch, t.M,
                                                            I, ids, tw, inv_w, delta, loss_part,
-                                                           npl, t.ppcb, npatch)));
+                                                           npl, t.ppcb, npatch,
+                                                           tm ? *tm : none, tm ? 1 : 0, err)));
   return e;
 }
 
