@@ -468,7 +468,7 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, bool refine = fals
       pty_handle::Mark m(h, PTY_K_ROWS_INV);
       CU(pty::launch_rows_inv(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
                               h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
-                              c0 > 0, h->stream));
+                              c0 > 0, h->tma_err, h->stream));
     }
     if (refine) {
       pty_handle::Mark m(h, PTY_K_REFINE);

@@ -70,6 +70,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* mb, unsign
   }
   return true;
 }
+// Bulk (TMA, no tensor map) copy of `bytes` (a multiple of 16; both
+// addresses 16-byte aligned) from global to shared memory, completing on mb.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* mb) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mb))
+      : "memory");
+}
 // 3-D tiled TMA load of the box at (x, y, z) of tensor map `tm` into dst.
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tm, int x, int y, int z,
                                             unsigned long long* mb) {

@@ -102,7 +102,7 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             float2* scratch, const float* omax_part,
                             const float* pmax_part, const float2* tw,
                             const UpdArgs& a, float2* pnum, float* pden,
-                            float* osum, int accumulate, cudaStream_t s);
+                            float* osum, int accumulate, int* err, cudaStream_t s);
 cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
                                const float* pden, const float* osum, int nslots,
                                float alpha_P, float reg_eps, float* pmax_part,

@@ -346,14 +346,30 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
 // Request (cp.async) patch slot lp's far-field rows [r0, r0 + R) of the M
 // modes into `zst` ([mode][row][column]) and its crop rows into `ost`.
 template <int W>
+// With `mbar`, thread 0 moves the far-field rows by bulk copies (one per
+// row, completing on the mbarrier); otherwise every thread issues 16-byte
+// cp.async copies.  The crop rows (any alignment) always take cp.async.
 PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 cc, int lp,
-                          int npl, int M, int R, int r0, float2* zst, float2* ost) {
-  constexpr int hw = W / 2;  // 16-byte chunks per row
-  for (int i = threadIdx.x; i < M * R * hw; i += blockDim.x) {
-    const int line = i / hw, h = i - line * hw;  // line = mode * R + row
-    const int k = line / R, r = line - k * R;
-    cp_async<16>(zst + line * W + 2 * h,
-                 scratch + (((size_t)lp * npl + k) * W + r0 + r) * W + 2 * h);
+                          int npl, int M, int R, int r0, float2* zst, float2* ost,
+                          unsigned long long* mbar) {
+  if (mbar) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async();  // the stage was just read through the generic proxy
+      mbar_expect_tx(mbar, (unsigned)(M * R * W * sizeof(float2)));
+      for (int line = 0; line < M * R; ++line) {  // line = mode * R + row
+        const int k = line / R, r = line - k * R;
+        bulk_load(zst + line * W, scratch + (((size_t)lp * npl + k) * W + r0 + r) * W,
+                  (unsigned)(W * sizeof(float2)), mbar);
+      }
+    }
+  } else {
+    constexpr int hw = W / 2;  // 16-byte chunks per row
+    for (int i = threadIdx.x; i < M * R * hw; i += blockDim.x) {
+      const int line = i / hw, h = i - line * hw;  // line = mode * R + row
+      const int k = line / R, r = line - k * R;
+      cp_async<16>(zst + line * W + 2 * h,
+                   scratch + (((size_t)lp * npl + k) * W + r0 + r) * W + 2 * h);
+    }
   }
   for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
     const int r = e / W, c = e - r * W;
@@ -373,9 +389,13 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
            const float* pmax_part, int n_pmax,
            const float2* __restrict__ tw_g, UpdArgs a,
            float2* pnum, float* pden,
-           float* osum, int accumulate, int npl, int refine, int bx, int by) {
+           float* osum, int accumulate, int npl, int refine, int bx, int by,
+           int* err = nullptr) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
+  __shared__ __align__(8) unsigned long long mbar_s;
+  unsigned long long* mbar = err ? &mbar_s : nullptr;  // bulk copies with error reporting
+  unsigned phase = 0;
   const int TB = max(M * R * G::LP, M * R * W);
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* tbuf = tw + W;             // transpose buffer, then D conj(P) terms
@@ -392,6 +412,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   const int nrb = W / R;
   pdl_trigger();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  if (mbar && threadIdx.x == 0) mbar_init(mbar, 1);
   pdl_wait();  // everything below is written by earlier kernels
   if (threadIdx.x < 32) {
     float m = 0.f;
@@ -442,13 +463,23 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   }
   __syncthreads();
   float osum_local = 0.f;
-  if (p0 < p1) rows_inv_stage<W>(scratch, O, Hx, scor[0], p0, npl, M, R, r0, zst, ostash);
+  if (p0 < p1)
+    rows_inv_stage<W>(scratch, O, Hx, scor[0], p0, npl, M, R, r0, zst, ostash, mbar);
   cp_async_commit();
   for (int lp = p0; lp < p1; ++lp) {
     const int2 cc = scor[lp - p0];
     const float2* oc = ostash + ((lp - p0) & 1) * R * W;
+    bool ok = true;
+    if (mbar) {
+      ok = mbar_wait_bounded(mbar, phase, 200000000ull);  // 0.2 s of the global timer
+      phase ^= 1;
+    }
     cp_async_wait<0>();
-    __syncthreads();  // this patch's rows have landed
+    if (__syncthreads_or(!ok)) {  // this patch's rows have landed, or the CTA leaves
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      if (!ok) mbar_wait_bounded(mbar, phase ^ 1, 200000000ull);  // the copy in flight
+      return;
+    }
     if (act && lane < G::N1) {
       float2 z[G::N2];
       const float2* src = zst + (k * R + r) * W;
@@ -459,7 +490,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     __syncthreads();  // the far-field stage is free: request the next patch
     if (lp + 1 < p1)
       rows_inv_stage<W>(scratch, O, Hx, scor[lp + 1 - p0], lp + 1, npl, M, R, r0, zst,
-                        ostash + ((lp + 1 - p0) & 1) * R * W);
+                        ostash + ((lp + 1 - p0) & 1) * R * W, mbar);
     cp_async_commit();
     float2 v[G::N1];
     if (act && lane < G::N2) inv_stepB<W>(v, lane, lbuf);

@@ -46,8 +46,10 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
            const float* __restrict__ pmax_part, int n_pmax,
            const float2* __restrict__ tw_g, UpdArgs a,
            float2* __restrict__ pnum, float* __restrict__ pden,
-           float* __restrict__ osum, int accumulate, int npl, int refine) {
-  rows_inv_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, scratch, omax_part, pmax_part, n_pmax, tw_g, a, pnum, pden, osum, accumulate, npl, refine, blockIdx.x, blockIdx.y);
+           float* __restrict__ osum, int accumulate, int npl, int refine, int* err) {
+  rows_inv_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, scratch, omax_part, pmax_part,
+                   n_pmax, tw_g, a, pnum, pden, osum, accumulate, npl, refine, blockIdx.x,
+                   blockIdx.y, err);
 }
 
 __global__ void __launch_bounds__(256)
@@ -475,14 +477,14 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             float2* scratch, const float* omax_part,
                             const float* pmax_part, const float2* tw,
                             const UpdArgs& a, float2* pnum, float* pden,
-                            float* osum, int accumulate, cudaStream_t s) {
+                            float* osum, int accumulate, int* err, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
   cudaError_t e = cudaSuccess;
   PTY_DISPATCH_W(t.W, e = launch_pdl(k_rows_inv<WW>, grid, dim3(t.thrC), t.smC, s, O, Hx, P,
                                      t.M, t.R, t.ppc, ids, corners, npatch, scratch, omax_part,
                                      pmax_part, t.n_pmax, tw, a, pnum, pden, osum, accumulate,
-                                     t.npl, t.refine));
+                                     t.npl, t.refine, err));
   return e;
 }
 
