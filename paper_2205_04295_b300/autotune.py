@@ -129,6 +129,8 @@ def apply(prob, table=None):
 
 def _workload(W, M):
     from . import synth
+    if W == 256 and M == 4:
+        return synth.sweep_256()  # the 40 000-position raster: its group sizes
     if W == 256:
         return synth.spiral_256()  # the full 10^4-position scan: its group sizes
     n = 14 if W <= 96 else 10
@@ -140,8 +142,8 @@ def main():
     import torch
     from . import synth
     ap = argparse.ArgumentParser()
-    ap.add_argument("--classes", default="256x5,64x1,64x2,64x3,96x1,96x2,96x3,128x1,128x2,"
-                                        "128x3,192x1,192x2,192x3")
+    ap.add_argument("--classes", default="256x5,256x4,64x1,64x2,64x3,96x1,96x2,96x3,128x1,"
+                                        "128x2,128x3,192x1,192x2,192x3")
     ap.add_argument("--out", default=CACHE)
     args = ap.parse_args()
     table = load(args.out)
