@@ -207,6 +207,18 @@ typedef struct {
 int pty_profile(pty_handle* h, int mode);
 int pty_get_stats(pty_handle* h, pty_stats* out, int reset);
 
+/* Test hook for the error path of the staged passes.  With on = 1 the
+ * mbarrier of every staged copy (the column pass's TMA loads, the inverse-row
+ * pass's bulk copies) expects one more arrival than the copies make: each
+ * copy still lands, but its bounded wait (0.2 s of the GPU's global timer)
+ * runs out, the CTA records the time-out in the handle's status word, waits
+ * (again bounded) for the copy it had in flight and leaves.  The next
+ * synchronising call (pty_run_iterations with err_out, a copy-out to host
+ * memory) returns PTY_ETIMEOUT and clears the word; the context stays usable,
+ * but the object and probe of the interrupted iteration are undefined until
+ * pty_set_data loads them again.  on = 0 restores normal operation.  Synchronises.  Nothing but tests should call this. */
+int pty_debug_stall_copies(pty_handle* h, int on);
+
 /* Differentiable forward model (bilinear crop at the exact float position,
  * Eqs. 1, 2, 4) with the amplitude loss
  *   L = sum_j sum_u (sqrt(sum_p |F(P_p o_j)|^2 + delta) - sqrt(I_j))^2

@@ -272,7 +272,8 @@ struct pty_handle {
   long long iter_launch[PTY_K_COUNT] = {0};
   long long iter_patches = 0;
   // tensor maps of the scratch for the column pass's TMA staging (plain and
-  // registration tilings); *tma_err is set by a TMA wait that timed out
+  // registration tilings); tma_err[0] is set by a wait of a staged pass that
+  // timed out, tma_err[1] is the stalled-copy test hook (pty_debug_stall_copies)
   CUtensorMap tmap_b{}, tmap_br{};
   bool tma_b = false, tma_br = false;
   int* tma_err = nullptr;
@@ -513,14 +514,15 @@ void remap_scratch(pty_handle* h) {
   h->tma_br = pty::encode_far_field_map(h->scratch, h->W, planes, h->tlr.CB, &h->tmap_br);
 }
 
-// A TMA wait in the column pass that timed out (reported at synchronising calls).
+// A wait of a staged pass (column pass TMA, inverse-row bulk copies) that
+// timed out (reported at synchronising calls).
 int check_tma_error(pty_handle* h) {
   int f = 0;
   CU(cudaMemcpyAsync(&f, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   if (f) {
     CU(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
-    return fail(PTY_ETIMEOUT, "a TMA copy of the column pass did not complete in time");
+    return fail(PTY_ETIMEOUT, "a staged copy (column or inverse-row pass) did not complete in time");
   }
   return PTY_OK;
 }
@@ -739,7 +741,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->P, (size_t)h->M * W2)) ||
       (rc = alloc_into(h, h->tw, (size_t)h->W)) ||
       (rc = alloc_into(h, h->scratch, scratch_elems)) ||
-      (rc = alloc_into(h, h->tma_err, (size_t)1)) ||
+      (rc = alloc_into(h, h->tma_err, (size_t)2)) ||
       (rc = alloc_into(h, h->cval, nparts)) ||
       (rc = alloc_into(h, h->cidx, nparts)) ||
       (rc = alloc_into(h, h->gap, (size_t)h->N)) ||
@@ -771,7 +773,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
   if (cudaMemcpyAsync(h->tw, tw.data(), sizeof(float2) * h->W, cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->err_part, 0, sizeof(float) * err_part_cap, h->stream) != cudaSuccess ||
-      cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->tma_err, 0, 2 * sizeof(int), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(PTY_ECUDA, "initial copies failed"));
@@ -1358,6 +1360,15 @@ int pty_profile(pty_handle* h, int mode) {
   if (!h) return fail(PTY_EINVAL, "null handle");
   if (mode != 0 && mode != 1) return fail(PTY_EINVAL, "profile mode %d", mode);
   h->prof_mode = mode;
+  return PTY_OK;
+}
+
+int pty_debug_stall_copies(pty_handle* h, int on) {
+  g_err.clear();
+  TRY(check_handle(h, false));
+  if (on != 0 && on != 1) return fail(PTY_EINVAL, "on=%d", on);
+  CU(cudaMemcpyAsync(h->tma_err + 1, &on, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
   return PTY_OK;
 }
 

@@ -70,6 +70,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* mb, unsign
   }
   return true;
 }
+// The library's status words: err[0] is set by a wait that gave up; err[1]
+// (0 or 1, written only by the host between calls) is a test hook that gives
+// a staged pass's mbarrier one more expected arrival, which no copy makes, so
+// that its bounded waits run out while every copy still completes.
+__device__ __forceinline__ int stalled_arrivals(const int* err) {
+  return err ? *reinterpret_cast<const volatile int*>(err + 1) : 0;
+}
 // Bulk (TMA, no tensor map) copy of `bytes` (a multiple of 16; both
 // addresses 16-byte aligned) from global to shared memory, completing on mb.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,

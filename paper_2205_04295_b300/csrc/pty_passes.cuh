@@ -229,7 +229,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
   unsigned phase = 0;
   pdl_trigger();
   for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) sids[t] = ids[p0 + t];
-  if (tma && threadIdx.x == 0) mbar_init(&mbar, 1);
+  if (tma && threadIdx.x == 0) mbar_init(&mbar, 1 + stalled_arrivals(err));
   pdl_wait();  // the far field comes from pass A
   __syncthreads();
   if constexpr (STAGE) {
@@ -379,8 +379,10 @@ PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 c
 
 // The next patch's far-field and crop rows are requested while the current
 // patch is transformed: no registers wait on global loads.  A lane always
-// owns the same W / N2 pixels of its (mode, row) line, so its probe values
-// and its probe-numerator sums stay in registers across the patches.
+// owns the same W / N2 pixels of its (mode, row) line, so its probe-numerator
+// sums stay in registers across the patches; its probe values are read from
+// the (cached, read-only) probe at use, which keeps the kernel within 128
+// registers without spilling (holding them too cost 5 % of this pass).
 template <int W>
 PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
            int R, int ppc, const int* __restrict__ ids,
@@ -412,7 +414,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   const int nrb = W / R;
   pdl_trigger();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
-  if (mbar && threadIdx.x == 0) mbar_init(mbar, 1);
+  if (mbar && threadIdx.x == 0) mbar_init(mbar, 1 + stalled_arrivals(err));
   pdl_wait();  // everything below is written by earlier kernels
   if (threadIdx.x < 32) {
     float m = 0.f;
@@ -439,15 +441,10 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
   const bool own = act && lane < G::N2;  // holds pixels c = N2 n1 + lane
-  float2 pk[G::N1], nm[G::N1];
-  {
-    const float2* prow = P + ((size_t)k * W + r0 + r) * W;
+  float2 nm[G::N1];
+  const float2* prow = P + ((size_t)k * W + r0 + r) * W;
 #pragma unroll
-    for (int n1 = 0; n1 < G::N1; ++n1) {
-      pk[n1] = own ? prow[G::N2 * n1 + lane] : make_float2(0.f, 0.f);
-      nm[n1] = make_float2(0.f, 0.f);
-    }
-  }
+  for (int n1 = 0; n1 < G::N1; ++n1) nm[n1] = make_float2(0.f, 0.f);
   const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
   // the CTA's corners and crop maxima max_r |o_j|^2 (reduced over the row
   // blocks of pass A), once: no dependent global loads inside the patch loop
@@ -501,8 +498,9 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
         const float2 o = oc[r * W + c];
-        const float2 D = csub(v[n1], cmul(pk[n1], o));
-        T[c] = cmulc(D, pk[n1]);
+        const float2 pkv = __ldg(prow + c);
+        const float2 D = csub(v[n1], cmul(pkv, o));
+        T[c] = cmulc(D, pkv);
         nm[n1] = cadd(nm[n1], cmulc(D, o));
       }
     }

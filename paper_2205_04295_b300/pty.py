@@ -86,6 +86,7 @@ _SIGS = {
     "pty_set_data": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "pty_set_data_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "pty_orthogonalize_probe": (c_int, [c_void_p, c_void_p]),
+    "pty_debug_stall_copies": (c_int, [c_void_p, c_int]),
     "pty_hermitian_eig": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
     "pty_set_scan_order": (c_int, [c_void_p, c_void_p]),
     "pty_run_iterations": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams), c_void_p]),
@@ -370,6 +371,11 @@ class Problem:
         check(lib().pty_loss_grad(self.h, O.data_ptr(), P.data_ptr(), pos.data_ptr(), float(delta),
                                   out.data_ptr(), gO.data_ptr(), gP.data_ptr(), gpos.data_ptr()))
         return out, gO, gP, gpos
+
+    def debug_stall_copies(self, on):
+        """Test hook: make every staged copy's bounded wait run out (on=True)
+        or restore normal operation (on=False)."""
+        check(lib().pty_debug_stall_copies(self.h, int(bool(on))))
 
     def orthogonalize_probe(self):
         """Orthogonalise the probe modes in place; returns their powers

@@ -326,3 +326,30 @@ def test_unfused_comparison_form_computes_the_same_iteration():
     u.iteration()
     assert rel_l2(u.O.cpu().numpy(), prob.object(False)) <= 1e-5
     assert rel_l2(u.P.cpu().numpy(), prob.probe(False)) <= 1e-5
+
+
+def test_stalled_copy_times_out_cleanly():
+    """The bounded waits of the staged passes: with the test hook on, every
+    staged copy's mbarrier expects one arrival that no copy makes, so the
+    waits run out (0.2 s each); the iteration ends with PTY_ETIMEOUT instead of
+    a hang, and the handle and the context stay usable afterwards."""
+    import time
+    from paper_2205_04295_b300 import pty
+    wl = synth.tiny(W=256, M=2, ny=2, nx=2, step=260.0, seed=31, photons=1e6)
+    d = build(wl)
+    prob = gpu_problem(wl, d)
+    prob.debug_stall_copies(True)
+    t0 = time.time()
+    with pytest.raises(pty.PtyError) as e:
+        prob.run(1)
+    assert e.value.code == pty.PTY_ETIMEOUT
+    assert time.time() - t0 < 20.0
+    prob.debug_stall_copies(False)
+    # reloaded, the same handle gives the oracle's first iteration
+    prob.set_data(d["I"], d["pos"], d["O0"], d["P0"])
+    eg = prob.run(1)[0]
+    st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+    eo = rpie.iterate(st, d["I"], rpie.RPIEParams())
+    assert rel_l2(prob.object(False), st.O) <= TOL1
+    assert rel_l2(prob.probe(False), st.P) <= TOL1
+    assert abs(eg - eo) <= 1e-5 * abs(eo)
