@@ -15,9 +15,14 @@
 // holds after forward step 3 and returning the natural-ordered samples a lane
 // held before forward step 1.  Nothing is normalised here; callers scale.
 //
-// Twiddles w_W^m = exp(-2 pi i m / W) come from a table computed on the host
-// in double precision and rounded to float.  The constants inside the small
-// DFTs (cos/sin of multiples of pi/8 and pi/6) are written out below.
+// Twiddles w_W^m = exp(-2 pi i m / W) come from a table of W entries computed
+// in double precision and rounded to float.  Slot e holds w_W^m with
+// m = tw_exponent(W, e): for a square factorisation (N1 = N2 = N) slot a N + b
+// holds w^{a b}, so that both steps read lane-consecutive slots (step 1 reads
+// w^{lane k1} at k1 N + lane, inverse step A w^{n2 lane} at n2 N + lane: no
+// shared-memory bank conflicts); otherwise slot m holds w^m.  The constants
+// inside the small DFTs (cos/sin of multiples of pi/8 and pi/6) are written
+// out below.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -158,6 +163,13 @@ template <bool INV> struct Dft<12, INV> {
   }
 };
 
+// N of a square factorisation W = N x N (0 if the factors differ).
+__host__ __device__ constexpr int tw_square(int W) { return W == 256 ? 16 : W == 64 ? 8 : 0; }
+// Exponent m of the twiddle w_W^m held in table slot e (0 <= e < W).
+__host__ __device__ constexpr int tw_exponent(int W, int e) {
+  return tw_square(W) ? (e / tw_square(W)) * (e % tw_square(W)) : e;
+}
+
 // Factorisation per supported pattern size.
 template <int W> struct Geo;
 template <> struct Geo<32> { static constexpr int N1 = 8, N2 = 4; };
@@ -176,6 +188,12 @@ template <int W> struct Line {
   static constexpr int RAW = W + W / N2;
   static constexpr int LP = RAW + ((20 - (RAW % 16)) % 16);
   static PTY_D int sp(int s) { return s + s / N2; }
+  static constexpr bool SQ = N1 == N2;
+  static_assert(tw_square(W) == (SQ ? N1 : 0), "twiddle layout and factorisation disagree");
+  // table slot of w^{lane k1} (forward step 1, lane = n2) and of w^{n2 lane}
+  // (inverse step A, lane = k1)
+  static PTY_D int twf(int k1, int lane) { return SQ ? k1 * N2 + lane : lane * k1; }
+  static PTY_D int twi(int n2, int lane) { return SQ ? n2 * N1 + lane : n2 * lane; }
 };
 
 // ---- forward step 1: v[n1] = x[N2 n1 + lane] on entry (lane < N2); leaves
@@ -186,7 +204,7 @@ PTY_D void fwd_step1(float2* v, int lane, const float2* tw, float2* buf) {
   Dft<G::N1, false>::run(v);
 #pragma unroll
   for (int k1 = 0; k1 < G::N1; ++k1) {
-    float2 t = k1 ? cmul(v[k1], tw[lane * k1]) : v[k1];
+    float2 t = k1 ? cmul(v[k1], tw[G::twf(k1, lane)]) : v[k1];
     buf[G::sp(G::N2 * k1 + lane)] = t;
   }
 }
@@ -207,7 +225,7 @@ PTY_D void inv_stepA(float2* z, int lane, const float2* tw, float2* buf) {
   Dft<G::N2, true>::run(z);
 #pragma unroll
   for (int n2 = 0; n2 < G::N2; ++n2) {
-    float2 t = n2 ? cmulc(z[n2], tw[n2 * lane]) : z[n2];
+    float2 t = n2 ? cmulc(z[n2], tw[G::twi(n2, lane)]) : z[n2];
     buf[G::sp(G::N2 * lane + n2)] = t;
   }
 }

@@ -52,7 +52,8 @@ Tiling make_tiling(int W, int M, bool refine = false, int max_threads_b = 512, i
 int lanes_per_line(int W);
 cudaError_t set_smem_limits(const Tiling& t);
 
-// Twiddle table w_W^m = exp(-2 pi i m / W), m = 0..W-1 (host, double -> float).
+// Twiddle table of the line FFTs: slot e holds w_W^m = exp(-2 pi i m / W) with
+// m = tw_exponent(W, e) (host, double -> float).
 void make_twiddles(int W, float2* out);
 
 // ---- the three passes of one chunk of a group -----------------------------

@@ -57,7 +57,7 @@ __device__ __forceinline__ bool na_corner(const float* pos, int j, int W, int Hy
 __device__ void na_twiddles(float2* tw, int W) {
   for (int e = threadIdx.x; e < W; e += blockDim.x) {
     double sn, cs;
-    sincospi(-2.0 * e / W, &sn, &cs);
+    sincospi(-2.0 * pty::tw_exponent(W, e) / W, &sn, &cs);
     tw[e] = make_float2((float)cs, (float)sn);
   }
 }

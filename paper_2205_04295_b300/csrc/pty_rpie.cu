@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(float2* __restrict__ data, int
   const int lines = blockDim.x / G::L;
   for (int e = threadIdx.x; e < W; e += blockDim.x) {
     double sn, cs;
-    sincospi(-2.0 * e / W, &sn, &cs);
+    sincospi(-2.0 * tw_exponent(W, e) / W, &sn, &cs);
     tw[e] = make_float2((float)cs, (float)sn);
   }
   __syncthreads();
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(float2* __restrict__ data, int
   float2* tbuf = tw + W;
   for (int e = threadIdx.x; e < W; e += blockDim.x) {
     double sn, cs;
-    sincospi(-2.0 * e / W, &sn, &cs);
+    sincospi(-2.0 * tw_exponent(W, e) / W, &sn, &cs);
     tw[e] = make_float2((float)cs, (float)sn);
   }
   __syncthreads();
@@ -407,9 +407,9 @@ cudaError_t set_smem_limits(const Tiling& t) {
 
 void make_twiddles(int W, float2* out) {
   const double pi = 3.14159265358979323846;
-  for (int m = 0; m < W; ++m) {
-    const double th = -2.0 * pi * (double)m / (double)W;
-    out[m] = make_float2((float)std::cos(th), (float)std::sin(th));
+  for (int e = 0; e < W; ++e) {
+    const double th = -2.0 * pi * (double)tw_exponent(W, e) / (double)W;
+    out[e] = make_float2((float)std::cos(th), (float)std::sin(th));
   }
 }
 
