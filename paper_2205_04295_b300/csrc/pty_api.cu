@@ -64,22 +64,41 @@ __global__ void k_sum_u16(const uint16_t* __restrict__ I, size_t n,
 // Copy patterns ids[0..n) (W2 counts each, W2 a multiple of 8) from host
 // memory the device can address (page-locked, unified addressing) into the
 // device stack, and add their counts to *sum (integers: exact in any order).
-// Reads cross the host link; one launch moves a whole group.
+// Reads cross the host link; one launch moves a whole group.  It runs beside
+// the passes, so it is kept small: 4 CTAs, each thread with 8 independent
+// 16-byte reads in flight (128 KB, enough to cover the link's latency at its
+// bandwidth); 64 CTAs with one read each took SM slots from the passes
+// (62.5 -> 59.3 ms for an end-to-end iteration of the 10^4-pattern spiral).
+constexpr int kGatherCtas = 4;
 __global__ void k_gather_host(uint16_t* __restrict__ dst, const uint16_t* __restrict__ src,
                               const int* __restrict__ ids, int n, int W2,
                               unsigned long long* sum) {
   const int per = W2 / 8;  // 16-byte vectors per pattern
   const long long total = (long long)n * per;
   unsigned long long s = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(i / per), e = (int)(i - (long long)p * per);
-    const size_t off = (size_t)ids[p] * W2;
-    const uint4 v = reinterpret_cast<const uint4*>(src + off)[e];
-    reinterpret_cast<uint4*>(dst + off)[e] = v;
-    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < total;
+       i0 += 8 * stride) {
+    uint4 v[8];
+    size_t o[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) s += (w[q] & 0xffffu) + (w[q] >> 16);
+    for (int u = 0; u < 8; ++u) {
+      const long long i = i0 + u * stride;
+      if (i < total) {
+        const int p = (int)(i / per), e = (int)(i - (long long)p * per);
+        o[u] = (size_t)ids[p] * W2 + (size_t)e * 8;
+        v[u] = *reinterpret_cast<const uint4*>(src + o[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (i0 + u * stride < total) {
+        *reinterpret_cast<uint4*>(dst + o[u]) = v[u];
+        const unsigned w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s += (w[q] & 0xffffu) + (w[q] >> 16);
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(sum, s);
@@ -576,7 +595,7 @@ int upload_groups(pty_handle* h, int g_end) {
     const int g = h->up_next;
     if (h->up_dev) {
       // one gather kernel per group, summing the counts on the way
-      k_gather_host<<<64, 256, 0, h->up_stream>>>(h->I, h->up_dev, h->gpos_d + h->gptr[g],
+      k_gather_host<<<kGatherCtas, 256, 0, h->up_stream>>>(h->I, h->up_dev, h->gpos_d + h->gptr[g],
                                                    h->gptr[g + 1] - h->gptr[g], (int)W2,
                                                    h->sum_d);
       CU(cudaGetLastError());

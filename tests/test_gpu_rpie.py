@@ -260,29 +260,32 @@ def test_device_inputs_equal_host_inputs():
     np.testing.assert_array_equal(a.probe(False), b.probe(False))
 
 
-def test_full_size_spiral_sampled_groups():
-    """Full 256x256, 5-mode, 10^4-position spiral, 2800^2 object, in the
-    launch configuration the benchmark times: run the first two groups on the
-    GPU and the same two groups in the oracle, then compare whole arrays."""
+def sampled_groups_parity(wl, n_groups):
+    """Full-size workload in the launch configuration the benchmark times (the
+    tuned tiling of its class): run the first n_groups groups on the GPU and
+    the same groups in the oracle, then compare whole arrays."""
     import torch
-    wl = synth.spiral_256()
+    from paper_2205_04295_b300 import autotune, pty
     d = synth.build(wl, device="cuda")
     I_dev = synth.counts_u16(d["I"])
-    from paper_2205_04295_b300 import pty
     prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
+    tuned = autotune.apply(prob)
+    assert tuned is not None
     prob.set_data(I_dev, torch.from_numpy(d["pos"]).cuda(), torch.from_numpy(d["O0"]).cuda(),
                   torch.from_numpy(d["P0"]).cuda())
-    groups = prob.groups()
-    sel = np.concatenate(groups[:2])
-    I_host = np.zeros((wl.N, wl.W, wl.W), np.uint16)
-    I_host[sel] = to_host(I_dev.to(torch.int32)[torch.from_numpy(sel).long().cuda()]).astype(np.uint16)
-    eg = prob.run_groups(0, 2)
+    groups = prob.groups()[:n_groups]
+    sel = np.concatenate(groups)
+    # the oracle sees only the selected patterns, re-indexed 0..len(sel)-1
+    I_sel = to_host(I_dev.to(torch.int32)[torch.from_numpy(sel).long().cuda()]).astype(np.uint16)
+    corners = model.crop_corners(d["pos"])[sel]
+    local = np.empty(wl.N, np.int64)
+    local[sel] = np.arange(len(sel))
+    eg = prob.run_groups(0, n_groups)
     st = rpie.State.create(d["O0"], d["P0"], d["pos"])
     err = 0.0
-    corners = model.crop_corners(d["pos"])
     po = rpie.RPIEParams()
-    for g in groups[:2]:
-        e, _, _ = rpie.rpie_group(st.O, st.P, I_host, corners, g, po)
+    for g in groups:
+        e, _, _ = rpie.rpie_group(st.O, st.P, I_sel, corners, local[g], po)
         err += e
     total = float(I_dev.to(torch.int64).sum().item())
     assert abs(eg - err / total) <= TOL1 * (err / total)
@@ -290,6 +293,19 @@ def test_full_size_spiral_sampled_groups():
     assert rel_l2(Og, st.O) <= TOL1
     assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= 2e-4
     assert rel_l2(prob.probe(False), st.P) <= TOL1
+    assert rel_l2(prob.probe(False) - d["P0"], st.P - d["P0"]) <= 2e-4
+    prob.close()
+
+
+def test_full_size_spiral_sampled_groups():
+    """256x256, 5 modes, 10^4-position spiral, 2800^2 object: first two groups."""
+    sampled_groups_parity(synth.spiral_256(), 2)
+
+
+def test_full_size_raster_sampled_groups():
+    """256x256, 4 modes, 40 000-position raster, 8192^2 object: first two
+    groups (about 280 patterns)."""
+    sampled_groups_parity(synth.sweep_256(), 2)
 
 
 def test_tiling_overrides_keep_parity_and_bad_ones_are_rejected():
