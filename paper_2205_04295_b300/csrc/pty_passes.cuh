@@ -185,6 +185,23 @@ PTY_D void cols_stage(const float2* scratch, const uint16_t* I, int j, int lp, i
   }
 }
 
+// Barrier over the threads of one mode's CB column lines (CB * L consecutive
+// threads: the transposes of a line never leave its mode).  Warp-aligned
+// groups of two or more warps take named barrier 1 + k; a warp, or groups
+// that tile a warp, __syncwarp (every thread of the warp calls it); anything
+// else the whole CTA.  With CB * L a multiple of 32 the launch has exactly
+// M * CB * L threads, so every participant of barrier 1 + k is in mode k.
+template <int W, int CB>
+PTY_D void mode_sync(int k) {
+  constexpr int n = CB * Line<W>::L;
+  if constexpr (n % 32 == 0 && n > 32)
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + k), "r"(n) : "memory");
+  else if constexpr (n == 32 || (n < 32 && 32 % n == 0))
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
 // GRAD = false: the modulus constraint (Eq. 7).  GRAD = true: the Fourier-
 // domain step of the amplitude-loss adjoint, G_Psi = 2 (1 - sqrt(I) / A) Psi
 // with A = sqrt(S + eps) (eps carries delta), and the loss partial sums.
@@ -243,17 +260,16 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
     if constexpr (STAGE) {
       bool ok = true;
       if (tma) {
+        // every thread waits on the mbarrier itself, so the TMA-written block
+        // is visible to it; its own count copies land with cp_async_wait (the
+        // others' are read after a later CTA barrier); the lines' buffers are
+        // free once the mode's threads have left the previous inverse step B
         ok = mbar_wait_bounded(&mbar, phase, 200000000ull);  // 0.2 s of the global timer
         phase ^= 1;
-      }
-      cp_async_wait<0>();
-      if (tma) {
-        if (__syncthreads_or(!ok)) {  // uniform: every thread leaves, none waits at a barrier
-          if (threadIdx.x == 0 && err) atomicExch(err, 1);
-          if (!ok) mbar_wait_bounded(&mbar, phase ^ 1, 200000000ull);  // the copy in flight
-          return;
-        }
+        cp_async_wait<0>();
+        mode_sync<W, CB>(k);
       } else {
+        cp_async_wait<0>();
         __syncthreads();  // this patch's block has landed
       }
       if (act && lane < G::N2) {
@@ -262,7 +278,18 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
         for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = srow[(G::N2 * n1 + lane) * CB];
         fwd_step1<W>(v, lane, tw, lbuf);
       }
-      __syncthreads();  // the stage is free: request the next patch
+      // the stage is free: request the next patch.  With TMA a wait that ran
+      // out makes every thread leave here (uniformly: none waits at a barrier
+      // afterwards); what it read from the stage is discarded.
+      if (tma) {
+        if (__syncthreads_or(!ok)) {
+          if (threadIdx.x == 0 && err) atomicExch(err, 1);
+          if (!ok) mbar_wait_bounded(&mbar, phase ^ 1, 200000000ull);  // the copy in flight
+          return;
+        }
+      } else {
+        __syncthreads();
+      }
       if (lp + 1 < p1)
         cols_stage<W, CB>(scratch, I, sids[lp + 1 - p0], lp + 1, npl, M, c0, stage,
                           cnt + ((lp + 1 - p0) & 1) * W * CB, tm, &mbar);
@@ -330,7 +357,12 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
         z[k2] = cscale(z[k2], Sb[(lane + G::N1 * k2) * CB + c]);
       inv_stepA<W>(z, lane, tw, lbuf);
     }
-    __syncthreads();
+    // the transpose stays within the mode's lines; the batched form (one
+    // patch per call, inside a persistent kernel) keeps the CTA barrier
+    if constexpr (STAGE)
+      mode_sync<W, CB>(k);
+    else
+      __syncthreads();
     if (act && lane < G::N2) {
       float2 v[G::N1];
       inv_stepB<W>(v, lane, lbuf);
