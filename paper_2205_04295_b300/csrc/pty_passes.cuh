@@ -61,6 +61,17 @@ PTY_D void rows_fwd_stage(const float2* O, int Hx, int2 cc, int R, int r0, float
   }
 }
 
+// Barrier over a row line's L lanes: they are consecutive threads, so where
+// lines tile warps (L = 8, 16) the warp suffices (every thread of the warp
+// calls it); L = 12 lines straddle warps and take the CTA barrier.
+template <int W>
+PTY_D void line_sync() {
+  if constexpr (32 % Line<W>::L == 0)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
 // The next patch's crop rows are requested while the current patch is
 // transformed (double-buffered in shared memory).
 template <int W>
@@ -76,7 +87,6 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   float2* tbuf = Prow + M * R * W;
   float2* ost = tbuf + (M + xo) * R * G::LP;  // 2 x R x W crop rows
   int2* scor = reinterpret_cast<int2*>(ost + 2 * R * W);  // ppc corners
-  __shared__ float red[32];
 
   const int r0 = bx * R;
   const int nrb = W / R;
@@ -86,6 +96,9 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) scor[t] = corners[ids[p0 + t]];
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   pdl_wait();  // O, P and the partial maxima belong to the previous kernels
+  // this row block's crop-maximum partials start at 0 (non-negative floats
+  // order as their bit patterns: the warps combine theirs by integer atomicMax)
+  for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) omax_part[(size_t)(p0 + t) * nrb + bx] = 0.f;
   __syncthreads();
   if (p0 < p1) rows_fwd_stage<W>(O, Hx, scor[0], R, r0, ost);
   cp_async_commit();
@@ -99,7 +112,6 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   const bool act = line < (M + xo) * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
-  const int nw = (blockDim.x + 31) >> 5;
   for (int lp = p0; lp < p1; ++lp) {
     cp_async_wait<0>();
     __syncthreads();  // this patch's crop rows have landed; lbuf is free
@@ -121,13 +133,9 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
       fwd_step1<W>(v, lane, tw, lbuf);
     }
     omax = warp_max(omax);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = omax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float m = 0.f;
-      for (int i = 0; i < nw; ++i) m = fmaxf(m, red[i]);
-      omax_part[(size_t)lp * nrb + bx] = m;
-    }
+    if ((threadIdx.x & 31) == 0 && omax > 0.f)
+      atomicMax(reinterpret_cast<int*>(omax_part + (size_t)lp * nrb + bx), __float_as_int(omax));
+    line_sync<W>();  // the transpose stays within the line
     if (act && lane < G::N1) {
       float2 z[G::N2];
       fwd_step3<W>(z, lane, lbuf);
@@ -550,8 +558,10 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
       den[e] += fmaf(1.f - a.beta, cabs2(o), a.beta * om);
     }
     osum_local += om;
-    __syncthreads();
+    // without registration the next patch's first barrier orders these reads
+    // of tbuf before its transpose writes
     if (refine) {
+      __syncthreads();  // onew
       // forward row DFTs of the refined crop o'_j -> plane M + 1 (XCORR_A)
       if (line < R && lane < G::N2) {
         float2 v2[G::N1];
