@@ -300,6 +300,7 @@ struct pty_handle {
   double* modes_G = nullptr;  // Gram matrix of the probe modes (M*M complex double)
   float2* modes_V = nullptr;  // their eigenvectors, as the mixing matrix
   float* err_slot = nullptr;  // the captured iteration's error
+  double* err_dpart = nullptr;  // the error reduction's per-CTA partial sums
   bool graphs_off = false;    // capture failed once: launch directly
   // A host pattern stack whose upload pty_set_data_async deferred: the next
   // pty_run_iterations copies it group by group on up_stream (one event per
@@ -761,6 +762,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->tw, (size_t)h->W)) ||
       (rc = alloc_into(h, h->scratch, scratch_elems)) ||
       (rc = alloc_into(h, h->tma_err, (size_t)2)) ||
+      (rc = alloc_into(h, h->err_dpart, (size_t)pty::kErrPartsMax)) ||
       (rc = alloc_into(h, h->cval, nparts)) ||
       (rc = alloc_into(h, h->cidx, nparts)) ||
       (rc = alloc_into(h, h->gap, (size_t)h->N)) ||
@@ -862,7 +864,8 @@ int iteration_graph(pty_handle* h, const pty_rpie_params* p) {
     for (int g = 0; g < G && rc == PTY_OK; ++g) rc = run_group(h, g, p);
     if (rc == PTY_OK) {
       pty_handle::Mark m(h, PTY_K_REDUCE);
-      e = pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_slot, h->stream);
+      e = pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_slot,
+                                 h->err_dpart, h->stream);
     }
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
     if (e == cudaSuccess) e = e2;
@@ -912,7 +915,7 @@ int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, floa
       {
         pty_handle::Mark m(h, PTY_K_REDUCE);
         CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter + it,
-                                  h->stream));
+                                  h->err_dpart, h->stream));
       }
       ++h->iter;
       continue;
@@ -933,7 +936,8 @@ int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p, floa
     for (int g = 0; g < G; ++g) TRY(run_group(h, g, p));
     {
       pty_handle::Mark m(h, PTY_K_REDUCE);
-      CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter + it, h->stream));
+      CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter + it,
+                                h->err_dpart, h->stream));
     }
     ++h->iter;
   }
@@ -989,7 +993,8 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
       // the partial sums of this iteration follow its column-pass tiling
       const size_t nerr = (size_t)h->N * (h->W / (on ? h->tlr.CB : h->tl.CB));
       pty_handle::Mark m(h, PTY_K_REDUCE);
-      CU(pty::launch_err_reduce(h->err_part, nerr, 0.0, h->sum_d, h->err_iter + it, h->stream));
+      CU(pty::launch_err_reduce(h->err_part, nerr, 0.0, h->sum_d, h->err_iter + it, h->err_dpart,
+                                h->stream));
     }
     if (on) {
       ++h->adam_t;
@@ -1130,7 +1135,8 @@ int pty_run_groups(pty_handle* h, int g_begin, int g_end, const pty_rpie_params*
   CU(cudaMemsetAsync(h->err_part, 0, sizeof(float) * h->err_part_n, h->stream));
   for (int g = g_begin; g < g_end; ++g) TRY(run_group(h, g, p));
   if (err_out) {
-    CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter, h->stream));
+    CU(pty::launch_err_reduce(h->err_part, h->err_part_n, 0.0, h->sum_d, h->err_iter,
+                              h->err_dpart, h->stream));
     CU(cudaMemcpyAsync(err_out, h->err_iter, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
   }

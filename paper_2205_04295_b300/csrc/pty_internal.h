@@ -119,8 +119,11 @@ int hermitian_eig(int M, const std::complex<double>* A, double* w, std::complex<
 cudaError_t launch_mix(float2* P, int M, int WW, const float2* V, cudaStream_t s);
 
 // Error normalised by 1/sum(I): inv_sumI, or the device sum when sum_dev != NULL.
+// tmp: kErrPartsMax doubles of device scratch.
+constexpr int kErrPartsMax = 296;
 cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
-                              const unsigned long long* sum_dev, float* out, cudaStream_t s);
+                              const unsigned long long* sum_dev, float* out, double* tmp,
+                              cudaStream_t s);
 cudaError_t launch_cols_intensity(const Tiling& t, const float2* scratch,
                                   const int* ids, int npatch, const float2* tw,
                                   float inv_w, float* out, cudaStream_t s);

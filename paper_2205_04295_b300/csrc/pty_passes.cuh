@@ -634,7 +634,8 @@ PTY_D void probe_apply_body(float2* P, int M, int WW, const float2* pnum, const 
 // reserved in the persistent kernel for every task).
 // The normalisation is 1 / sum(I): inv_sumI, or, when sum_dev is given, the
 // device-resident counts sum (so that no host value waits for an upload).
-PTY_D void err_reduce_body(const float* part, size_t n, double inv_sumI,
+template <typename T>
+PTY_D void err_reduce_body(const T* part, size_t n, double inv_sumI,
                            const unsigned long long* sum_dev, float* out) {
   extern __shared__ float4 smem4[];
   double* red = reinterpret_cast<double*>(smem4);

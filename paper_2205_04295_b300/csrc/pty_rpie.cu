@@ -72,8 +72,29 @@ k_pmax(const float2* __restrict__ P, int M, int WW, float* __restrict__ pmax_par
   if (threadIdx.x == 0) pmax_part[blockIdx.x] = lmax;
 }
 
-__global__ void __launch_bounds__(1024)
-k_err_reduce(const float* __restrict__ part, size_t n, double inv_sumI,
+// The iteration's error: kErrParts CTAs each sum a fixed contiguous range of
+// the per-(pattern, column block) partials in double (fixed order), then one
+// CTA sums their kErrParts results in order and normalises.  Deterministic;
+// one CTA over all 10^4 x 64 partials took 0.38 ms per iteration.
+constexpr int kErrParts = kErrPartsMax;
+__global__ void __launch_bounds__(256)
+k_err_partial(const float* __restrict__ part, size_t n, double* __restrict__ out) {
+  __shared__ double red[256];
+  const size_t per = (n + gridDim.x - 1) / gridDim.x;
+  const size_t b0 = (size_t)blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
+  double s = 0.0;
+  for (size_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += (double)part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256)
+k_err_reduce(const double* __restrict__ part, size_t n, double inv_sumI,
              const unsigned long long* sum_dev, float* out) {
   err_reduce_body(part, n, inv_sumI, sum_dev, out);
 }
@@ -502,8 +523,10 @@ cudaError_t launch_pmax(const Tiling& t, const float2* P, float* pmax_part, cuda
 }
 
 cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
-                              const unsigned long long* sum_dev, float* out, cudaStream_t s) {
-  k_err_reduce<<<1, 1024, 1024 * sizeof(double), s>>>(err_part, n, inv_sumI, sum_dev, out);
+                              const unsigned long long* sum_dev, float* out, double* tmp,
+                              cudaStream_t s) {
+  k_err_partial<<<kErrParts, 256, 0, s>>>(err_part, n, tmp);
+  k_err_reduce<<<1, 256, 256 * sizeof(double), s>>>(tmp, kErrParts, inv_sumI, sum_dev, out);
   return cudaGetLastError();
 }
 
