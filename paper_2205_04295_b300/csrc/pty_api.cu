@@ -1095,7 +1095,7 @@ int grad_run(pty_handle* h, const void* Ov, const void* Pv, const float* pos, fl
   pty_handle::Mark m(h, PTY_K_GRAD);
   CU(pty::launch_grad_finish(h->tl, used, h->pnum, adjoint ? static_cast<float2*>(gPv) : nullptr,
                              h->gpos_part, h->N, adjoint ? gpos : nullptr, h->err_part,
-                             h->err_part_n, loss, h->stream));
+                             h->err_part_n, loss, h->err_dpart, h->stream));
   return PTY_OK;
 }
 }  // namespace

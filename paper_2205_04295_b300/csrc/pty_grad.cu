@@ -315,27 +315,27 @@ __global__ void k_grad_sum_probe(const float2* __restrict__ part, int nslots, si
     gP[i] = s;
   }
 }
-__global__ void k_grad_sum_pos(const float* __restrict__ part, int nrb, int N,
+// dL/dpos_j: the row blocks' partial (y, x) pairs of position j, one warp per
+// position (coalesced), each lane summing a fixed strided subset in order,
+// then a fixed shuffle tree: deterministic.
+__global__ void k_grad_sum_pos(const float2* __restrict__ part, int nrb, int N,
                                float* __restrict__ gpos) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * N) return;
-  const int j = i >> 1, ax = i & 1;
-  float s = 0.f;
-  for (int b = 0; b < nrb; ++b) s += part[((size_t)j * nrb + b) * 2 + ax];
-  gpos[i] = s;
-}
-__global__ void __launch_bounds__(1024)
-k_grad_sum_loss(const float* __restrict__ part, size_t n, float* out) {
-  __shared__ double red[1024];
-  double s = 0.0;
-  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)part[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), l = threadIdx.x & 31;
+  if (j >= N) return;  // whole warps
+  float sy = 0.f, sx = 0.f;
+  for (int b = l; b < nrb; b += 32) {
+    const float2 v = part[(size_t)j * nrb + b];
+    sy += v.x;
+    sx += v.y;
   }
-  if (threadIdx.x == 0) *out = (float)red[0];
+  for (int o = 16; o > 0; o >>= 1) {
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+  }
+  if (l == 0) {
+    gpos[2 * j] = sy;
+    gpos[2 * j + 1] = sx;
+  }
 }
 
 }  // namespace
@@ -430,13 +430,17 @@ cudaError_t launch_grad_scatter(int W, int M, float2* gO, int Hx, const int* ids
 cudaError_t launch_grad_finish(const Tiling& t, int nslots, const float2* gP_part, float2* gP,
                                const float* gpos_part, int N, float* gpos,
                                const float* loss_part, size_t nloss, float* loss,
-                               cudaStream_t s) {
+                               double* tmp, cudaStream_t s) {
   const size_t n = (size_t)t.M * t.W * t.W;
   if (gP) k_grad_sum_probe<<<(int)std::min<size_t>(1184, (n + 255) / 256), 256, 0, s>>>(
       gP_part, nslots, n, gP);
-  if (gpos) k_grad_sum_pos<<<(2 * N + 255) / 256, 256, 0, s>>>(gpos_part, t.W / t.R, N, gpos);
-  k_grad_sum_loss<<<1, 1024, 0, s>>>(loss_part, nloss, loss);
-  return cudaGetLastError();
+  if (gpos)
+    k_grad_sum_pos<<<(int)(((size_t)N * 32 + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const float2*>(gpos_part), t.W / t.R, N, gpos);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the loss: the same two-level fixed-order double sum as the iteration error
+  return launch_err_reduce(loss_part, nloss, 1.0, nullptr, loss, tmp, s);
 }
 
 }  // namespace pty

@@ -95,7 +95,7 @@ cudaError_t launch_grad_scatter(int W, int M, float2* gO, int Hx, const int* ids
 cudaError_t launch_grad_finish(const Tiling& t, int nslots, const float2* gP_part, float2* gP,
                                const float* gpos_part, int N, float* gpos,
                                const float* loss_part, size_t nloss, float* loss,
-                               cudaStream_t s);
+                               double* tmp, cudaStream_t s);
 cudaError_t set_grad_smem(const Tiling& t);
 
 cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
