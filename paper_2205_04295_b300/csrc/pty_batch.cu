@@ -55,7 +55,7 @@ template <int W>
 __device__ __noinline__ void batch_rows_inv(const BatchProb& pb, const BatchTask& tk) {
   const int* ids = pb.gpos + tk.ids_off;
   for (int bx = tk.x0; bx < tk.x1; ++bx) {
-    rows_inv_body<W>(pb.O, pb.Hx, pb.P, pb.M, pb.R, pb.ppc, ids, pb.corners, tk.npatch,
+    rows_inv_body<W, true>(pb.O, pb.Hx, pb.P, pb.M, pb.R, pb.ppc, ids, pb.corners, tk.npatch,
                      pb.scratch, pb.omax_part, pb.pmax_part, pb.n_pmax, pb.tw, pb.a, pb.pnum,
                      pb.pden, pb.osum, tk.flag, pb.M, 0, bx, tk.y);
     __syncthreads();
