@@ -209,6 +209,55 @@ def host_inputs_for_groups(wl, n_groups):
             "P0": synth.initial_probe(P)}
 
 
+def _oracle_worker(d, groups, budget_s, start, q):
+    """One process of the all-core oracle figure: its own copy of the state,
+    whole groups of the selected patterns in order (cycling), timed after every
+    process is ready."""
+    single_thread_env()
+    from oracle import rpie
+    st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+    prm = rpie.RPIEParams()
+    start.wait()
+    done, t0, i = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s:
+        g = groups[i % len(groups)]
+        rpie.rpie_group(st.O, st.P, d["I"], d["corners"], g, prm)
+        done += len(g)
+        i += 1
+    q.put((done, time.perf_counter() - t0))
+
+
+def oracle_all_cores(wl, nproc, budget_s, n_groups=8):
+    """Aggregate oracle throughput of `nproc` concurrent FP64 processes, each
+    running the oracle unchanged on its own copy of the state over the first
+    n_groups whole groups (a bound on what splitting the work across processes
+    could reach: the groups of one iteration depend on each other)."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import grouping, model
+    d = host_inputs_for_groups(wl, n_groups)
+    groups = grouping.greedy_groups(d["pos"].astype(np.float64), wl.W)[:n_groups]
+    sel = np.concatenate(groups)
+    local = np.empty(wl.N, np.int64)
+    local[sel] = np.arange(len(sel))
+    dd = {"I": d["I"][sel], "corners": model.crop_corners(d["pos"])[sel], "pos": d["pos"],
+          "O0": d["O0"], "P0": d["P0"]}
+    lg = [local[g] for g in groups]
+    ctx = mp.get_context("spawn")
+    start, q = ctx.Barrier(nproc), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(dd, lg, budget_s, start, q)) for _ in range(nproc)]
+    for p in ps:
+        p.start()
+    res = [q.get() for _ in ps]
+    for p in ps:
+        p.join()
+    patches = sum(r[0] for r in res)
+    return {"value": sum(r[0] / r[1] for r in res), "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": "%d concurrent FP64 processes, each on its own copy of the state over the "
+                      "first %d groups (%d patches in all, %.1f s each)"
+                      % (nproc, n_groups, patches, budget_s)}
+
+
 def single_thread_env():
     for v in ("OMP_NUM_THREADS", "MKL_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
         os.environ.setdefault(v, "1")
@@ -237,7 +286,9 @@ def run_reference(args, wl):
             "config": {"workload": wl.name, "W": wl.W, "M": wl.M, "N": wl.N, "object": [wl.Hy, wl.Hx]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            **({"cpu_all_cores": oracle_all_cores(wl, args.oracle_procs, per_step)}
+               if args.oracle_procs > 0 else {})}
 
 
 # --------------------------------------------------------------------- ours
@@ -476,6 +527,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--oracle-procs", type=int, default=0,
+                    help="with --impl reference: also time this many concurrent oracle processes")
     args = ap.parse_args()
     wl = workloads()[args.workload]()
 
