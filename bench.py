@@ -424,6 +424,8 @@ def run_ours(args, wl, rank, world, local):
     ortho_ms = (time.perf_counter() - t0) / 5 * 1e3
 
     batch = run_batch_measure(args, dev) if not args.no_batch else None
+    # measured FP32 FMA throughput, beside the nominal peak (after the timed work)
+    ffma = pty.measure_fp32_peak()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -440,6 +442,8 @@ def run_ours(args, wl, rank, world, local):
                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                         "traffic_unit": "DRAM bytes per launch (warm L2, scaled from ncu)",
                         "peak_source": "148 SM x 128 FP32 lanes x 2 x 2032 MHz",
+                        "peak_measured": ffma, "frac_of_measured": achieved / ffma if ffma else None,
+                        "peak_measured_source": "FMA-chain kernel (pty_measure_fp32_peak)",
                         "share": kst["ms"][dom] / total_ms},
            "kernel_ms": {k: kst["ms"][k] for k in kinds},
            "kernel_launches": {k: kst["launches"][k] for k in kinds},

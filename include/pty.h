@@ -316,6 +316,12 @@ int pty_group_positions(const float* pos, int N, int W, int max_group,
  * the FFT alone).  inverse = 0: exp(-2 pi i ...), 1: exp(+2 pi i ...). */
 int pty_fft2(void* data, int W, int batch, int inverse, void* stream);
 
+/* Measured FP32 FMA throughput of the current device in TFLOP/s (eight
+ * independent FMA chains per thread, 8 CTAs of 256 threads per SM, best of
+ * three timed launches): the measured counterpart of the nominal FP32 peak
+ * the passes' roofline uses.  Allocates and frees about 1 MB; synchronises. */
+int pty_measure_fp32_peak(double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

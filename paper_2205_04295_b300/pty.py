@@ -87,6 +87,7 @@ _SIGS = {
     "pty_set_data_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "pty_orthogonalize_probe": (c_int, [c_void_p, c_void_p]),
     "pty_debug_stall_copies": (c_int, [c_void_p, c_int]),
+    "pty_measure_fp32_peak": (c_int, [c_void_p]),
     "pty_hermitian_eig": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
     "pty_set_scan_order": (c_int, [c_void_p, c_void_p]),
     "pty_run_iterations": (c_int, [c_void_p, c_int, ctypes.POINTER(RpieParams), c_void_p]),
@@ -147,6 +148,13 @@ def lib():
 def check(rc):
     if rc != PTY_OK:
         raise PtyError(rc, lib().pty_last_error().decode())
+
+
+def measure_fp32_peak():
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    check(lib().pty_measure_fp32_peak(ctypes.byref(v)))
+    return v.value
 
 
 # ------------------------------------------------------------ marshalling

@@ -20,3 +20,12 @@ def test_fft2_matches_numpy(W, inverse):
     want = np.fft.ifft2(xx) * W * W if inverse else np.fft.fft2(xx)
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err < 2e-6, err
+
+
+def test_fp32_peak_measurement_is_plausible():
+    """The FMA-chain measurement lands between a third of and just above the
+    nominal peak (148 SMs x 128 lanes x 2 flop x 2.032 GHz = 77.0 TFLOP/s;
+    the clock may sit below its maximum)."""
+    from paper_2205_04295_b300 import pty
+    t = pty.measure_fp32_peak()
+    assert 25.0 < t < 80.0
