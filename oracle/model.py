@@ -76,3 +76,15 @@ def model_intensities(O, P, pos):
     for j, c in enumerate(corners):
         out[j] = to_detector(model_intensity_unshifted(P, crop(O, c, W)))
     return out
+
+
+def canvas_map(P, corners, shape):
+    """Scan density on the object ("canvas map", the M-rPIE discussion around
+    Fig. 5): the summed probe intensity sum_j sum_p |P_p(r - c_j)|^2 that the
+    positions deposit on each object pixel."""
+    W = P.shape[-1]
+    p2 = np.sum(np.abs(P) ** 2, axis=0)
+    C = np.zeros(shape, dtype=np.float64)
+    for cy, cx in np.asarray(corners, dtype=np.int64):
+        C[cy:cy + W, cx:cx + W] += p2
+    return C
