@@ -24,10 +24,15 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
   rows_fwd_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, tw_g, scratch, omax_part, npl, xo, blockIdx.x, blockIdx.y);
 }
 
-// 384 threads, two CTAs per SM: at most 80 registers a thread.  With use_tma
-// the far-field block is staged by TMA through `tmap` (a time-out sets *err).
-template <int W, int CB, bool GRAD>
-__global__ void __launch_bounds__(384, 2)
+// Two CTAs per SM.  BIG launches up to 384 threads and holds 80 registers a
+// thread; the others launch at most 320 threads (M * CB * lanes <= 320, e.g.
+// 5 modes x 4 columns x 16 lanes) and may hold 96, which removes the spills
+// of the 80-register build (22.2 -> 21.4 ms per iteration at 256², 5 modes).
+// With use_tma the far-field block is staged by TMA through `tmap` (a
+// time-out sets *err).
+constexpr int kColsSmall = 320;  // threads of the 96-register column kernels
+template <int W, int CB, bool GRAD, bool BIG>
+__global__ void __launch_bounds__(BIG ? 384 : kColsSmall, 2)
 k_cols(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
@@ -414,8 +419,10 @@ cudaError_t set_smem_limits(const Tiling& t) {
     e = allow_max_smem((const void*)k_rows_fwd<WW>);
     for (int cb = 2; cb <= 16 && e == cudaSuccess; cb *= 2) {
       PTY_DISPATCH_CB(cb, {
-        e = allow_max_smem((const void*)k_cols<WW, CBB, false>);
-        if (e == cudaSuccess) e = allow_max_smem((const void*)k_cols<WW, CBB, true>);
+        e = allow_max_smem((const void*)k_cols<WW, CBB, false, false>);
+        if (e == cudaSuccess) e = allow_max_smem((const void*)k_cols<WW, CBB, true, false>);
+        if (e == cudaSuccess) e = allow_max_smem((const void*)k_cols<WW, CBB, false, true>);
+        if (e == cudaSuccess) e = allow_max_smem((const void*)k_cols<WW, CBB, true, true>);
       });
     }
     if (e == cudaSuccess)
@@ -469,9 +476,15 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   cudaError_t e = cudaSuccess;
   CUtensorMap none{};
-  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = launch_pdl(k_cols<WW, CBB, false>, grid,
-                                                           dim3(t.thrB), t.smB, s, scratch, t.M,
-                                                           I, ids, tw, inv_w, eps, err_part,
+  const bool big = t.thrB > kColsSmall;
+  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = big ? launch_pdl(k_cols<WW, CBB, false, true>,
+                                                           grid, dim3(t.thrB), t.smB, s, scratch,
+                                                           t.M, I, ids, tw, inv_w, eps, err_part,
+                                                           t.npl, t.ppcb, npatch,
+                                                           tm ? *tm : none, tm ? 1 : 0, err)
+                                                    : launch_pdl(k_cols<WW, CBB, false, false>,
+                                                           grid, dim3(t.thrB), t.smB, s, scratch,
+                                                           t.M, I, ids, tw, inv_w, eps, err_part,
                                                            t.npl, t.ppcb, npatch,
                                                            tm ? *tm : none, tm ? 1 : 0, err)));
   return e;
@@ -485,10 +498,16 @@ cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   cudaError_t e = cudaSuccess;
   CUtensorMap none{};
-  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = launch_pdl(k_cols<WW, CBB, true>, grid,
-                                                           dim3(t.thrB), t.smB, s, scratch, t.M,
-                                                           I, ids, tw, inv_w, delta, loss_part,
-                                                           npl, t.ppcb, npatch,
+  const bool big = t.thrB > kColsSmall;
+  PTY_DISPATCH_W(t.W, PTY_DISPATCH_CB(t.CB, e = big ? launch_pdl(k_cols<WW, CBB, true, true>,
+                                                           grid, dim3(t.thrB), t.smB, s, scratch,
+                                                           t.M, I, ids, tw, inv_w, delta,
+                                                           loss_part, npl, t.ppcb, npatch,
+                                                           tm ? *tm : none, tm ? 1 : 0, err)
+                                                    : launch_pdl(k_cols<WW, CBB, true, false>,
+                                                           grid, dim3(t.thrB), t.smB, s, scratch,
+                                                           t.M, I, ids, tw, inv_w, delta,
+                                                           loss_part, npl, t.ppcb, npatch,
                                                            tm ? *tm : none, tm ? 1 : 0, err)));
   return e;
 }
