@@ -407,7 +407,7 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
           128;                        // alignment of the stage
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
-  t.smC = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + M * R * W) * sizeof(float2) +
+  t.smC = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + 2 * M * R * W) * sizeof(float2) +
           (size_t)2 * R * W * sizeof(float) + (size_t)t.ppc * (sizeof(int2) + sizeof(float));
   t.n_pmax = std::max(1, std::min(1024, W * W / 256));
   return t;
