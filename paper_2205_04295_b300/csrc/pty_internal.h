@@ -27,6 +27,8 @@ struct Tiling {
   int thrA, thrB, thrC;
   size_t smA, smB, smC, smI;  // dynamic shared memory (bytes)
   int n_pmax;    // CTAs of the probe-apply kernel (= partial maxima)
+  int pstage;    // 1: pass C copies its probe rows to shared memory (when that
+                 // costs it no CTA per SM), 0: reads them through L1 at use
 };
 
 bool supported_W(int W);

@@ -420,14 +420,16 @@ PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 c
 // The next patch's far-field and crop rows are requested while the current
 // patch is transformed: no registers wait on global loads.  A lane always
 // owns the same W / N2 pixels of its (mode, row) line, so its probe-numerator
-// sums stay in registers across the patches; its probe values are read at use
-// from the CTA's probe rows, copied to shared memory once in the prologue
-// (the probe is constant during the pass), which keeps the kernel within 128
-// registers without spilling (holding them in registers cost 5 % of this
-// pass, reading them through L1 at use 5 %).  PK_REG holds them in registers
-// anyway: the batched form's task function, compiled on its own, measured
-// 1-2.5 % faster that way.
-template <int W, bool PK_REG = false>
+// sums stay in registers across the patches; its probe values are read at use,
+// which keeps the kernel within 128 registers without spilling (holding them
+// in registers cost 5 % of this pass).  With PSTAGE they come from the CTA's
+// probe rows, copied to shared memory once in the prologue (the probe is
+// constant during the pass; 5 % faster than reading them through L1 at use),
+// which the tiling turns on only where the extra shared memory costs no CTA
+// per SM (at 256², 4 modes it would cost one: 15 % slower).  PK_REG holds
+// them in registers anyway: the batched form's task function, compiled on
+// its own, measured 1-2.5 % faster that way.
+template <int W, bool PK_REG = false, bool PSTAGE = false>
 PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
            int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
@@ -448,8 +450,8 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   float2* ostash = tbuf + TB;        // 2 x R x W: crop rows, double-buffered
   float2* onew = ostash + 2 * R * W; // refined crop rows (refine only)
   float2* zst = onew + (refine ? R * W : 0);  // M x R x W far-field rows
-  float2* prs = zst + M * R * W;     // M x R x W probe rows (constant in the pass)
-  float* invd = reinterpret_cast<float*>(prs + M * R * W);  // alpha_O / denominator
+  float2* prs = zst + M * R * W;     // M x R x W probe rows (PSTAGE only)
+  float* invd = reinterpret_cast<float*>(prs + (PSTAGE ? M * R * W : 0));  // alpha_O / den.
   float* den = invd + R * W;
   int2* scor = reinterpret_cast<int2*>(den + R * W);         // ppc corners
   float* som = reinterpret_cast<float*>(scor + ppc);         // ppc crop maxima
@@ -476,7 +478,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
       float s = 0.f;
       for (int k = 0; k < M; ++k) {
         const float2 p = P[((size_t)k * W + r0 + rr) * W + c];
-        if constexpr (!PK_REG) prs[(k * R + rr) * W + c] = p;
+        if constexpr (PSTAGE) prs[(k * R + rr) * W + c] = p;
         s += cabs2(p);
       }
       const float dn = fmaf(1.f - a.gamma, s, gden);
@@ -550,7 +552,13 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
         const float2 o = oc[r * W + c];
-        const float2 pkv = PK_REG ? pk[n1] : prs[(k * R + r) * W + c];
+        float2 pkv;
+        if constexpr (PK_REG)
+          pkv = pk[n1];
+        else if constexpr (PSTAGE)
+          pkv = prs[(k * R + r) * W + c];
+        else
+          pkv = __ldg(prow + c);
         const float2 D = csub(v[n1], cmul(pkv, o));
         T[c] = cmulc(D, pkv);
         nm[n1] = cadd(nm[n1], cmulc(D, o));

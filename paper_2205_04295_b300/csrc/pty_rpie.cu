@@ -42,7 +42,7 @@ k_cols(float2* __restrict__ scratch, int M,
                          blockIdx.x, blockIdx.y, use_tma ? &tmap : nullptr, err);
 }
 
-template <int W>
+template <int W, bool PSTAGE>
 __global__ void __launch_bounds__(256, 2)
 k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
            int R, int ppc, const int* __restrict__ ids,
@@ -52,9 +52,9 @@ k_rows_inv(float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
            const float2* __restrict__ tw_g, UpdArgs a,
            float2* __restrict__ pnum, float* __restrict__ pden,
            float* __restrict__ osum, int accumulate, int npl, int refine, int* err) {
-  rows_inv_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, scratch, omax_part, pmax_part,
-                   n_pmax, tw_g, a, pnum, pden, osum, accumulate, npl, refine, blockIdx.x,
-                   blockIdx.y, err);
+  rows_inv_body<W, false, PSTAGE>(O, Hx, P, M, R, ppc, ids, corners, npatch, scratch, omax_part,
+                                  pmax_part, n_pmax, tw_g, a, pnum, pden, osum, accumulate, npl,
+                                  refine, blockIdx.x, blockIdx.y, err);
 }
 
 __global__ void __launch_bounds__(256)
@@ -364,6 +364,30 @@ bool supported_W(int W) {
     default: return cudaErrorInvalidValue;            \
   }
 
+// Pass C may copy its probe rows to shared memory only where that costs it no
+// CTA per SM: the occupancy of k_rows_inv<W> at thr threads with sm0 and with
+// sm1 bytes of dynamic shared memory (false if it cannot be queried).
+bool pstage_pays(int W, int thr, size_t sm0, size_t sm1) {
+  const void *f0 = nullptr, *f1 = nullptr;
+  switch (W) {
+    case 32: f0 = (const void*)k_rows_inv<32, false>; f1 = (const void*)k_rows_inv<32, true>; break;
+    case 64: f0 = (const void*)k_rows_inv<64, false>; f1 = (const void*)k_rows_inv<64, true>; break;
+    case 96: f0 = (const void*)k_rows_inv<96, false>; f1 = (const void*)k_rows_inv<96, true>; break;
+    case 128: f0 = (const void*)k_rows_inv<128, false>; f1 = (const void*)k_rows_inv<128, true>; break;
+    case 192: f0 = (const void*)k_rows_inv<192, false>; f1 = (const void*)k_rows_inv<192, true>; break;
+    case 256: f0 = (const void*)k_rows_inv<256, false>; f1 = (const void*)k_rows_inv<256, true>; break;
+    default: return false;
+  }
+  int n0 = 0, n1 = 0;
+  if (allow_max_smem(f0) != cudaSuccess || allow_max_smem(f1) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, f0, thr, sm0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, f1, thr, sm1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n1 > 0 && n1 >= n0;
+}
+
 Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, int ppc_req,
                    int CB_req) {
   Tiling t{};
@@ -407,8 +431,12 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
           128;                        // alignment of the stage
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
-  t.smC = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + 2 * M * R * W) * sizeof(float2) +
-          (size_t)2 * R * W * sizeof(float) + (size_t)t.ppc * (sizeof(int2) + sizeof(float));
+  const size_t smC0 = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + M * R * W) *
+                          sizeof(float2) +
+                      (size_t)2 * R * W * sizeof(float) + (size_t)t.ppc * (sizeof(int2) + sizeof(float));
+  const size_t smC1 = smC0 + (size_t)M * R * W * sizeof(float2);
+  t.pstage = pstage_pays(W, t.thrC, smC0, smC1) ? 1 : 0;
+  t.smC = t.pstage ? smC1 : smC0;
   t.n_pmax = std::max(1, std::min(1024, W * W / 256));
   return t;
 }
@@ -426,7 +454,9 @@ cudaError_t set_smem_limits(const Tiling& t) {
       });
     }
     if (e == cudaSuccess)
-      e = allow_max_smem((const void*)k_rows_inv<WW>);
+      e = allow_max_smem((const void*)k_rows_inv<WW, false>);
+    if (e == cudaSuccess)
+      e = allow_max_smem((const void*)k_rows_inv<WW, true>);
     if (e == cudaSuccess)
       e = allow_max_smem((const void*)k_cols_intensity<WW>);
   });
@@ -521,10 +551,13 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
   cudaError_t e = cudaSuccess;
-  PTY_DISPATCH_W(t.W, e = launch_pdl(k_rows_inv<WW>, grid, dim3(t.thrC), t.smC, s, O, Hx, P,
-                                     t.M, t.R, t.ppc, ids, corners, npatch, scratch, omax_part,
-                                     pmax_part, t.n_pmax, tw, a, pnum, pden, osum, accumulate,
-                                     t.npl, t.refine, err));
+  PTY_DISPATCH_W(t.W, e = t.pstage
+      ? launch_pdl(k_rows_inv<WW, true>, grid, dim3(t.thrC), t.smC, s, O, Hx, P, t.M, t.R, t.ppc,
+                   ids, corners, npatch, scratch, omax_part, pmax_part, t.n_pmax, tw, a, pnum,
+                   pden, osum, accumulate, t.npl, t.refine, err)
+      : launch_pdl(k_rows_inv<WW, false>, grid, dim3(t.thrC), t.smC, s, O, Hx, P, t.M, t.R,
+                   t.ppc, ids, corners, npatch, scratch, omax_part, pmax_part, t.n_pmax, tw, a,
+                   pnum, pden, osum, accumulate, t.npl, t.refine, err));
   return e;
 }
 
