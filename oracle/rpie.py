@@ -12,7 +12,7 @@ P the estimates at the start of the group:
         Psi_p    = F psi_p                                          (Eq. 2)
         S_j      = sum_p |Psi_p|^2
         err     += sum_u (sqrt(S_j) - sqrt(I_j))^2
-        Psi'_p   = sqrt(I_j) Psi_p / (sqrt(S_j) + eps)              (Eq. 7, reading R1)
+        Psi'_p   = sqrt(I_j) Psi_p / (sqrt(S_j) + eps)              (Eq. 7, detector plane)
         D_p      = F^-1 Psi'_p - psi_p
         o'       = o + alpha_O sum_p D_p conj(P_p)
                          / (gamma Pmax + (1-gamma) Pint + reg_eps Pmax)   (Eq. 6)
@@ -21,7 +21,10 @@ P the estimates at the start of the group:
         [refine] s_j = peak of xcorr(o, o'),  g_j = -s_j
     P_p += alpha_P num_p / (den + reg_eps sum_j max|o_j|^2)         (Eq. 5, ratio of sums)
 
-Readings: eps is taken at the one-photon amplitude level (eps = 1 by
+Readings: Eq. 7 as printed applies sqrt(I) to the exit-plane wave and sums
+over positions; it is read as the usual modulus constraint in the detector
+plane, every mode scaled by sqrt(I_j) over the root of the summed mode
+intensities.  eps is taken at the one-photon amplitude level (eps = 1 by
 default): with eps -> 0 the constrained wave at a detector pixel where the
 model is (numerically) dark but photons were counted has full amplitude and
 the phase of rounding noise, so the iteration stops being a continuous
