@@ -249,10 +249,12 @@ int pty_model_intensities(pty_handle* h, float* dst, int mem_kind);
  * PTY_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * process exit.  One pattern needs M*W*W*8 bytes of it; larger requests fail
  * with PTY_EINVAL.  All calls share that array, so calls overlapping on the
- * GPU race; serialise them.  The first call on each device resolves the
- * array's device address (cudaGetSymbolAddress) and should come before any
- * stream capture.  A pattern whose crop box leaves the object is written as
- * NaN. */
+ * GPU race; serialise them.  Every call resolves the array's device address
+ * afresh (cudaGetSymbolAddress in the context current at the call; nothing
+ * is cached, so a device reset or a caller's own driver context is safe).
+ * The first call in a context may load the library's module and should come
+ * before any stream capture.  A pattern whose crop box leaves the object is
+ * written as NaN. */
 #define PTY_NOALLOC_SCRATCH_BYTES ((size_t)6 << 20)
 int pty_model_intensities_noalloc(const void* O, int Hy, int Hx, const void* P,
                                   int M, int W, const float* pos, int N,

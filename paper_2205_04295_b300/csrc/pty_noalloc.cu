@@ -17,24 +17,23 @@
 // to start at zero.
 //
 // Host code never dereferences the array's symbol (on the host it is only a
-// stand-in, not a device address): the device address is resolved once per
-// device with cudaGetSymbolAddress, on the first call made with that device
-// current, and passed to the kernels.  That first call therefore also runs a
-// couple of CUDA runtime queries and should be made before any stream capture.
+// stand-in, not a device address): every call resolves the device address
+// with cudaGetSymbolAddress in the context current at the call and passes it
+// to the kernels.  The lookup allocates nothing and costs about a
+// microsecond; it is not cached, because an address belongs to the module as
+// loaded in one context, and a cache keyed on the device number would go
+// stale after cudaDeviceReset or under a caller's own (non-primary) driver
+// context on the same device.  The first call in a context may make the
+// runtime load the library's module there, so it should come before any
+// stream capture.
 #include "pty_fft.cuh"
 #include "pty_internal.h"
 #include "../../include/pty.h"
-
-#include <mutex>
 
 namespace {
 
 constexpr size_t kScratchElems = PTY_NOALLOC_SCRATCH_BYTES / sizeof(float2);
 static __device__ __align__(256) float2 g_noalloc_scratch[kScratchElems];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float2* g_addr[kMaxDevices] = {nullptr};
 
 int pow2_floor(int v) {
   int p = 1;
@@ -204,22 +203,12 @@ extern "C" int pty_model_intensities_noalloc(const void* O, int Hy, int Hx, cons
                           "one %dx%d pattern with %d modes needs %zu bytes of far-field scratch; "
                           "the fixed no-allocation scratch holds %zu",
                           W, W, M, need, (size_t)PTY_NOALLOC_SCRATCH_BYTES);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return pty::set_error(PTY_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return pty::set_error(PTY_EINVAL, "device index %d", dev);
-  float2* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess)
-        return pty::set_error(PTY_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      g_addr[dev] = static_cast<float2*>(p);
-    }
-    scratch = g_addr[dev];
-  }
+  // the address in the context current now (see the top of this file)
+  void* addr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+  if (e != cudaSuccess || !addr)
+    return pty::set_error(PTY_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  float2* scratch = static_cast<float2*>(addr);
   const float2* Oc = static_cast<const float2*>(O);
   const float2* Pc = static_cast<const float2*>(P);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
