@@ -18,7 +18,8 @@ P the estimates at the start of the group:
                          / (gamma Pmax + (1-gamma) Pint + reg_eps Pmax)   (Eq. 6)
         write o' back into O (disjoint boxes: no conflicts)
         num_p   += D_p conj(o);  den += beta max|o|^2 + (1-beta)|o|^2
-        [refine] s_j = peak of xcorr(o, o'),  g_j = -s_j
+        [refine] s_j = peak of xcorr(o, o')  (XCORR_A; XCORR_B: xcorr(S_j, I_j)),
+                 g_j = -s_j
     P_p += alpha_P num_p / (den + reg_eps sum_j max|o_j|^2)         (Eq. 5, ratio of sums)
 
 Readings: Eq. 7 as printed applies sqrt(I) to the exit-plane wave and sums
@@ -72,6 +73,7 @@ class RefineParams:
     eps: float = 1e-8
     start_iter: int = 0       # first iteration (0-based, global) that refines
     max_step: float = 0.0     # per-axis clamp of one Adam step, 0 = none
+    point: str = "A"          # where the error signal is taken (Fig. 2): "A" or "B"
 
 
 @dataclass
@@ -95,8 +97,18 @@ class State:
                    last_shift=np.zeros_like(pos), gap=np.ones(len(pos)))
 
 
-def rpie_group(O, P, I, corners, members, prm, U=0):
+def rpie_group(O, P, I, corners, members, prm, U=0, point="A"):
     """Update O (in place) for every position of one group and P at its end.
+
+    With U > 0 every position's registration shift is measured at ``point``
+    (the two switch positions of the refinement scheme, Fig. 2):
+
+    * "A" (XCORR_A): the crop o_j before its update against the refined crop
+      o'_j, in the object plane (complex images);
+    * "B" (XCORR_B): the model intensity S_j = sum_p |Psi_p|^2 of the current
+      estimate against the measured intensity I_j, in the detector plane
+      (real images), both in the unshifted layout (a common circular shift
+      of the two images does not move a circular correlation peak).
 
     Returns (error numerator, shifts (len(members), 2), gaps).
     """
@@ -116,7 +128,8 @@ def rpie_group(O, P, I, corners, members, prm, U=0):
         psi = P * o[None]
         Psi = F(psi)
         S = np.sum(np.abs(Psi) ** 2, axis=0)
-        sqI = np.sqrt(from_detector(np.asarray(I[j], dtype=np.float64)))
+        Ij = from_detector(np.asarray(I[j], dtype=np.float64))
+        sqI = np.sqrt(Ij)
         err += float(np.sum((np.sqrt(S) - sqI) ** 2))
         Psi_c = Psi * (sqI / (np.sqrt(S) + prm.eps))[None]
         D = Finv(Psi_c) - psi
@@ -129,7 +142,10 @@ def rpie_group(O, P, I, corners, members, prm, U=0):
         den += prm.beta * om + (1.0 - prm.beta) * a2
         omax_sum += om
         if U:
-            shifts[i], gap = xcorr_peak(o, o_new, U)
+            if point == "A":
+                shifts[i], gap = xcorr_peak(o, o_new, U)
+            else:
+                shifts[i], gap = xcorr_peak(S, Ij, U)
             gaps.append(gap)
     if prm.update_probe:
         pden = np.broadcast_to(den + prm.reg_eps * omax_sum, num.shape)
@@ -159,7 +175,8 @@ def iterate(state, I, prm, rfn=None, order=None, groups=None):
     err = 0.0
     g_meas = np.zeros_like(state.pos)
     for members in groups:
-        e, sh, gaps = rpie_group(state.O, state.P, I, corners, members, prm, U)
+        e, sh, gaps = rpie_group(state.O, state.P, I, corners, members, prm, U,
+                                 rfn.point if refine_on else "A")
         err += e
         if refine_on:
             g_meas[members] = -sh

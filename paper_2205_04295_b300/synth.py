@@ -16,7 +16,8 @@ Poisson draw, which uses a torch.Generator with the same seed):
 * object: amplitude = periodic Gaussian-smoothed (sigma 2 px) uniform noise
   min-max mapped to [0.5, 1]; phase = independent smoothed noise mapped to
   [-pi/2, pi/2];
-* probe: circular aperture of radius R = 3W/8 times exp(i 4 pi (r/R)^2);
+* probe: circular aperture of radius R = 3W/8 times exp(i c (r/R)^2), c = 4 pi
+  unless a workload says otherwise (c = 0: a flat-phase, focused probe);
   modes = base x {1, x/R, y/R, xy/R^2, (x^2-y^2)/R^2}, Gram-Schmidt
   orthogonalised, mode powers = occupancy x photons per pattern;
 * data: I_j = clip(Poisson(sum_p |DFT(P_p(r - f_j) O(t_j + r))|^2), 0, 65535),
@@ -47,6 +48,7 @@ class Workload:
     upsample: int = 20
     lr: float = 0.5
     seed: int = 0
+    probe_curv: float = 4.0 * math.pi   # probe phase at the aperture edge (radians)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -74,13 +76,13 @@ def make_object(Hy, Hx, rng):
     return (amp * np.exp(1j * ph)).astype(np.complex64)
 
 
-def make_probe(W, M, photons, occupancy):
+def make_probe(W, M, photons, occupancy, curv=4.0 * math.pi):
     R = 3.0 * W / 8.0
     c = (W - 1) / 2.0
     y, x = np.mgrid[0:W, 0:W].astype(np.float64)
     y, x = y - c, x - c
     r2 = (x * x + y * y) / (R * R)
-    base = (r2 <= 1.0) * np.exp(1j * 4.0 * np.pi * r2)
+    base = (r2 <= 1.0) * np.exp(1j * curv * r2)
     shapes = [np.ones_like(x), x / R, y / R, x * y / R ** 2, (x * x - y * y) / R ** 2]
     # further modes (up to 16): more monomials x^a y^b / R^(a+b), by degree
     for a_, b_ in ((2, 0), (2, 1), (1, 2), (3, 0), (0, 3), (2, 2), (3, 1), (1, 3), (4, 0),
@@ -173,7 +175,7 @@ def build(wl, device="cpu"):
     view stored as int16 bits -- see ``counts_u16``)."""
     rng = np.random.Generator(np.random.PCG64(wl.seed))
     O = make_object(wl.Hy, wl.Hx, rng)
-    P = make_probe(wl.W, wl.M, wl.photons, wl.occupancy)
+    P = make_probe(wl.W, wl.M, wl.photons, wl.occupancy, wl.probe_curv)
     cnt, clipped = simulate_counts(O, P, wl.pos_true, wl.seed, device=device)
     return dict(O_true=O, P_true=P, I=cnt, clipped=clipped,
                 O0=np.ones((wl.Hy, wl.Hx), dtype=np.complex64),

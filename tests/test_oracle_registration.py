@@ -23,7 +23,7 @@ def shifted(a, d):
     return np.fft.ifft2(np.fft.fft2(a) * ph)
 
 
-DT = [np.complex64, np.complex128]
+DT = [np.float32, np.float64]   # resolution of the argmax decision
 
 
 @pytest.mark.parametrize("dt", DT)
@@ -73,7 +73,7 @@ def test_matches_zero_padded_brute_force():
         c = np.abs(np.fft.ifft2(big)) ** 2
         n = np.unravel_index(np.argmax(c), c.shape)
         want = np.array([registration.wrap(n[0], U * W), registration.wrap(n[1], U * W)]) / U
-        s, _ = registration.xcorr_peak(a, b, U, np.complex128)
+        s, _ = registration.xcorr_peak(a, b, U, np.float64)
         np.testing.assert_allclose(s, want, atol=1e-12)
 
 
@@ -114,3 +114,33 @@ def test_refinement_moves_an_offset_position_toward_the_truth():
         rpie.iterate(st, I, prm, rfn)
     e1 = np.abs(st.pos[0] - true[0])
     assert np.all(e1 < e0)
+
+
+def _shift_real(a, d):
+    """Real image a(r + d), circular, by the Fourier shift theorem."""
+    return np.real(shifted(a, d))
+
+
+@pytest.mark.parametrize("d", [(1.0, -2.0), (0.35, 0.8), (-1.55, 0.05)])
+def test_xcorr_b_measures_the_detector_plane_shift(d):
+    """XCORR_B correlates the model intensity S_j with the measured I_j.  When
+    the measured pattern is the model's own intensity moved by d (a 1/U-grid
+    shift), one refining group must report g_j = d exactly; a swapped pair
+    of images (planted) would report -d."""
+    U = 20
+    rng = np.random.default_rng(6)
+    W, H = 32, 40
+    O = 0.7 + 0.3 * smooth_patch(H, rng, sigma=2.0)
+    P = smooth_patch(W, rng, sigma=3.0)[None] * 40.0
+    corner = np.array([[3, 5]])
+    S = model.model_intensities(O, P, corner)[0]            # detector layout
+    d = np.array(d)
+    I = np.clip(_shift_real(S, d), 0.0, None)[None]   # counts are non-negative
+    prm = rpie.RPIEParams(alpha_O=0.0, alpha_P=0.0)
+    _, sh, gaps = rpie.rpie_group(O.copy(), P.copy(), I, corner, [0], prm, U, point="B")
+    np.testing.assert_allclose(-sh[0], d, atol=1e-9)
+    # consistent data: XCORR_B finds no shift, and neither does XCORR_A (with
+    # zero step sizes it compares o_j with itself)
+    for point in ("A", "B"):
+        _, sh0, _ = rpie.rpie_group(O.copy(), P.copy(), S[None], corner, [0], prm, U, point=point)
+        np.testing.assert_allclose(sh0[0], 0.0, atol=1e-12)
