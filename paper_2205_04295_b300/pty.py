@@ -225,16 +225,78 @@ def fft2_(x, inverse=False):
     return x
 
 
-class Problem:
-    """One reconstruction problem (a pty_handle) on the current CUDA device."""
+class TorchAllocator:
+    """The handle's device memory from PyTorch's caching allocator, through
+    the alloc/free hooks of pty_problem_desc: the library's buffers then share
+    torch's memory pool (no cudaMalloc, no implicit synchronisation on reuse)
+    and are accounted in torch.cuda.memory_allocated().
 
-    def __init__(self, W, M, N, Hy, Hx, stream=None, scratch_bytes=0):
+    ``fail_after`` (test hook, host side): after that many successful
+    allocations every further request returns NULL, which the library must
+    report as PTY_ENOMEM.  ``live`` maps each outstanding pointer to its size.
+    Keep the allocator referenced for as long as any handle it serves lives.
+    """
+
+    def __init__(self, device=None, fail_after=None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.fail_after = fail_after
+        self.n_alloc = 0
+        self.live = {}
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.free_fn = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, stream, ctx):
+        if self.fail_after is not None and self.n_alloc >= self.fail_after:
+            return None
+        try:
+            import torch
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+        except Exception:   # out of memory: the library returns PTY_ENOMEM
+            return None
+        self.n_alloc += 1
+        self.live[p] = int(nbytes)
+        return p
+
+    def _free(self, ptr, stream, ctx):
+        if ptr is None:
+            return
+        self.live.pop(ptr, None)
+        try:
+            import torch
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:   # interpreter shutdown: torch is already gone
+            pass
+
+    def hooks(self):
+        return self.alloc_fn, self.free_fn
+
+
+def _hooks(allocator):
+    """(alloc, free, keep-alive) for a desc: "torch" (default), "cuda" (the
+    library's own cudaMalloc) or a TorchAllocator-like object."""
+    if allocator == "cuda":
+        return ALLOC_FN(), FREE_FN(), None
+    if allocator == "torch":
+        allocator = TorchAllocator()
+    a, f = allocator.hooks()
+    return a, f, allocator
+
+
+class Problem:
+    """One reconstruction problem (a pty_handle) on the current CUDA device.
+
+    Device memory comes from PyTorch's caching allocator by default
+    (``allocator="torch"``); ``"cuda"`` lets the library call cudaMalloc."""
+
+    def __init__(self, W, M, N, Hy, Hx, stream=None, scratch_bytes=0, allocator="torch"):
         import torch
         self.W, self.M, self.N, self.Hy, self.Hx = W, M, N, Hy, Hx
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        d = ProblemDesc(W, M, N, Hy, Hx, c_void_p(stream.cuda_stream), ALLOC_FN(), FREE_FN(),
+        af, ff, self._allocator = _hooks(allocator)
+        d = ProblemDesc(W, M, N, Hy, Hx, c_void_p(stream.cuda_stream), af, ff,
                         None, scratch_bytes, 0)
         h = c_void_p()
         check(lib().pty_init_problem(ctypes.byref(d), ctypes.byref(h)))
@@ -430,16 +492,17 @@ class _Borrowed(Problem):
 class Batch:
     """Many independent problems run by one persistent graph-captured launch."""
 
-    def __init__(self, shapes, stream=None, scratch_bytes=0):
+    def __init__(self, shapes, stream=None, scratch_bytes=0, allocator="torch"):
         import torch
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
         n = len(shapes)
+        af, ff, self._allocator = _hooks(allocator)
         arr = (ProblemDesc * n)()
         for i, (W, M, N, Hy, Hx) in enumerate(shapes):
-            arr[i] = ProblemDesc(W, M, N, Hy, Hx, c_void_p(stream.cuda_stream), ALLOC_FN(),
-                                 FREE_FN(), None, scratch_bytes, 0)
+            arr[i] = ProblemDesc(W, M, N, Hy, Hx, c_void_p(stream.cuda_stream), af, ff, None,
+                                 scratch_bytes, 0)
         b = c_void_p()
         check(lib().pty_batch_create(arr, n, ctypes.byref(b)))
         self.b = b
