@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define PTY_ABI_VERSION 1
+#define PTY_ABI_VERSION 2
 
 enum {
   PTY_OK = 0,
@@ -94,7 +94,13 @@ typedef struct {
   float eps;       /* Adam denominator guard */
   int start_iter;  /* first iteration (counted over the handle's life) that refines */
   float max_step;  /* per-axis clamp of one step; 0 = none */
+  int point;       /* where the error signal is taken (Fig. 2): PTY_XCORR_A (0),
+                      the crop o_j against its update o'_j in the object plane;
+                      PTY_XCORR_B (1), the model intensity sum_p |Psi_p|^2
+                      against the measured counts I_j in the detector plane */
 } pty_refine_params;
+
+enum { PTY_XCORR_A = 0, PTY_XCORR_B = 1 };
 
 /* Message describing the last failure on this thread ("" if none). */
 const char* pty_last_error(void);
@@ -138,11 +144,13 @@ int pty_set_scan_order(pty_handle* h, const int32_t* order);
 int pty_run_iterations(pty_handle* h, int n_iter, const pty_rpie_params* p,
                        float* err_out);
 
-/* n_iter iterations with XCORR_A registration of every updated crop and an
- * Adam step of every position at the end of each iteration (once the
- * handle's iteration count reaches r->start_iter).  Positions are clamped to
- * keep the crops inside O.  shift_out (host, N*2, may be NULL) receives the
- * last measured shift g_j = -argmax xcorr(o_j, o'_j). */
+/* n_iter iterations with registration of every position and an Adam step
+ * of every position at the end of each iteration (once the handle's
+ * iteration count reaches r->start_iter); r->point picks XCORR_A (the crop
+ * before and after its update) or XCORR_B (model against measured
+ * detector-plane intensity), the two switch positions of Fig. 2.  Positions
+ * are clamped to keep the crops inside O.  shift_out (host, N*2, may be
+ * NULL) receives the last measured shift g_j = -argmax xcorr(a_j, b_j). */
 int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
                          const pty_refine_params* r, float* err_out,
                          float* shift_out);

@@ -464,7 +464,8 @@ pty::UpdArgs upd_args(const pty_rpie_params* p) {
   return pty::UpdArgs{p->alpha_O, p->alpha_P, p->beta, p->gamma, p->eps, p->reg_eps};
 }
 
-int run_group(pty_handle* h, int g, const pty_rpie_params* p, bool refine = false) {
+// refine: 0 = plain, 1 = XCORR_A, 2 = XCORR_B registration of every patch
+int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0) {
   const int n = h->gptr[g + 1] - h->gptr[g];
   const int* ids = h->gpos_d + h->gptr[g];
   const pty::UpdArgs a = upd_args(p);
@@ -483,16 +484,20 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, bool refine = fals
       CU(pty::launch_cols(tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps,
                           h->err_part,
                           refine ? (h->tma_br ? &h->tmap_br : nullptr) : (h->tma_b ? &h->tmap_b : nullptr),
-                          h->tma_err, h->stream));
+                          h->tma_err, h->stream, refine == 2 ? h->M : -1));
     }
     {
       pty_handle::Mark m(h, PTY_K_ROWS_INV);
       CU(pty::launch_rows_inv(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
                               h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
-                              c0 > 0, h->tma_err, h->stream));
+                              c0 > 0, h->tma_err, h->stream, refine == 1 ? 1 : 0));
     }
     if (refine) {
       pty_handle::Mark m(h, PTY_K_REFINE);
+      if (refine == 2) {
+        CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
+        h->n_launch[PTY_K_REFINE] += 1;
+      }
       CU(pty::launch_xcorr_cols(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
       CU(pty::launch_xcorr_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->cval, h->cidx,
                                 h->stream));
@@ -958,7 +963,8 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
   if (n_iter < 0) return fail(PTY_EINVAL, "n_iter < 0");
   if (r->upsample < 1 || r->upsample > 40) return fail(PTY_EINVAL, "upsample %d outside 1..40", r->upsample);
   if (!std::isfinite(r->lr) || !(r->b1 >= 0.f && r->b1 < 1.f) || !(r->b2 >= 0.f && r->b2 < 1.f) ||
-      !(r->eps >= 0.f) || !(r->max_step >= 0.f) || r->start_iter < 0)
+      !(r->eps >= 0.f) || !(r->max_step >= 0.f) || r->start_iter < 0 ||
+      (r->point != PTY_XCORR_A && r->point != PTY_XCORR_B))
     return fail(PTY_EINVAL, "bad refine parameters");
   if (r->upsample != h->roots_U) {
     h->rg = pty::make_refgeo(h->W, r->upsample);
@@ -988,7 +994,8 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
     const bool on = h->iter >= r->start_iter;
     if (on) CU(pty::set_smem_limits(h->tlr));
     const int G = (int)h->gptr.size() - 1;
-    for (int g = 0; g < G; ++g) TRY(run_group(h, g, p, on));
+    const int mode = on ? (r->point == PTY_XCORR_B ? 2 : 1) : 0;
+    for (int g = 0; g < G; ++g) TRY(run_group(h, g, p, mode));
     {
       // the partial sums of this iteration follow its column-pass tiling
       const size_t nerr = (size_t)h->N * (h->W / (on ? h->tlr.CB : h->tl.CB));

@@ -68,11 +68,13 @@ cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx,
                                   int npatch, const float2* tw, float2* scratch,
                                   float* omax_part, cudaStream_t s);
 // tm (may be NULL): tensor map of the scratch for TMA staging (see
-// encode_far_field_map); a TMA wait that times out sets *err.
+// encode_far_field_map); a TMA wait that times out sets *err.  xb >= 0
+// (XCORR_B): also write the model intensity and the counts into scratch
+// planes xb, xb + 1.
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
                         float eps, float* err_part, const CUtensorMap* tm, int* err,
-                        cudaStream_t s);
+                        cudaStream_t s, int xb = -1);
 // Fourier-domain step of the gradient (amplitude loss, delta-smoothed).
 cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I,
                              const int* ids, int npatch, const float2* tw, float inv_w,
@@ -105,7 +107,8 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             float2* scratch, const float* omax_part,
                             const float* pmax_part, const float2* tw,
                             const UpdArgs& a, float2* pnum, float* pden,
-                            float* osum, int accumulate, int* err, cudaStream_t s);
+                            float* osum, int accumulate, int* err, cudaStream_t s,
+                            int refine = -1);  // -1: t.refine; 0: no o'_j row DFTs
 cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
                                const float* pden, const float* osum, int nslots,
                                float alpha_P, float reg_eps, float* pmax_part,
@@ -129,7 +132,7 @@ cudaError_t launch_err_reduce(const float* err_part, size_t n, double inv_sumI,
 cudaError_t launch_cols_intensity(const Tiling& t, const float2* scratch,
                                   const int* ids, int npatch, const float2* tw,
                                   float inv_w, float* out, cudaStream_t s);
-// ---- XCORR_A registration and the Adam step (pty_refine.cu) ---------------
+// ---- XCORR_A / XCORR_B registration and the Adam step (pty_refine.cu) ------
 struct RefGeo {
   int W, U, K;   // fine grid K = ceil(1.5 U) points per axis
   int CBX, RX;   // columns / rows per CTA of the correlation passes
@@ -140,6 +143,9 @@ RefGeo make_refgeo(int W, int U);
 cudaError_t set_refine_smem(const RefGeo& g);
 // roots exp(+2 pi i n / (U W)), n = 0..U W - 1 (host, double -> float)
 void make_up_roots(int W, int U, float2* out);
+// XCORR_B: forward row DFTs of planes M, M + 1 (model intensity, counts).
+cudaError_t launch_xcorrb_rows(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
+                               const float2* tw, cudaStream_t s);
 cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
                               const float2* tw, cudaStream_t s);
 cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, int M,

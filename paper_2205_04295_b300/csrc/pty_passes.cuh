@@ -210,7 +210,9 @@ PTY_D void mode_sync(int k) {
     __syncthreads();
 }
 
-// GRAD = false: the modulus constraint (Eq. 7).  GRAD = true: the Fourier-
+// GRAD = false: the modulus constraint (Eq. 7); with xb >= 0 (XCORR_B
+// registration) also the model intensity S = sum_p |Psi_p|^2 and the counts,
+// written unshifted into the real parts of scratch planes xb and xb + 1.  GRAD = true: the Fourier-
 // domain step of the amplitude-loss adjoint, G_Psi = 2 (1 - sqrt(I) / A) Psi
 // with A = sqrt(S + eps) (eps carries delta), and the loss partial sums.
 // The next patch's column block is requested while the current one is
@@ -225,7 +227,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
        float* __restrict__ err_part, int npl, int ppcb, int npatch, int bx, int by,
-       const void* tm = nullptr, int* err = nullptr) {
+       const void* tm = nullptr, int* err = nullptr, int xb = -1) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   __shared__ __align__(8) unsigned long long mbar;
@@ -343,6 +345,13 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
           const float d = a - sI;
           e = fmaf(d, d, e);
           Sb[u * CB + cl] = sI / (a + eps) * f2;
+          if (xb >= 0) {
+            // XCORR_B: the model intensity and the counts, unshifted, as the
+            // real parts of scratch planes xb and xb + 1
+            float2* pl = scratch + ((size_t)lp * npl + xb) * W * W + (size_t)u * W + c0 + cl;
+            pl[0] = make_float2(s * f2, 0.f);
+            pl[(size_t)W * W] = make_float2((float)cn[el], 0.f);
+          }
         } else {
           const float a = sqrtf(fmaf(s, f2, eps));
           const float d = a - sI;

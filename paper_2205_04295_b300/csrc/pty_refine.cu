@@ -1,11 +1,15 @@
-// XCORR_A registration and the Adam position step (Adam-based position
-// refinement section of Guzzi et al., arXiv 2205.04295; Eqs. 8-9,
-// Algorithm 1; registration after Guizar-Sicairos, Thurman & Fienup,
-// Opt. Lett. 33, 156, 2008).
+// XCORR_A / XCORR_B registration and the Adam position step (Adam-based
+// position refinement section of Guzzi et al., arXiv 2205.04295; Eqs. 8-9,
+// Algorithm 1, the two switch positions of Fig. 2; registration after
+// Guizar-Sicairos, Thurman & Fienup, Opt. Lett. 33, 156, 2008).
 //
 // For each patch of a group, after pass C, the scratch holds
-//   plane M     : row DFTs of o_j       (crop before the update; pass A)
-//   plane M + 1 : row DFTs of o'_j      (refined crop; pass C)
+//   XCORR_A: plane M     : row DFTs of o_j   (crop before the update; pass A)
+//            plane M + 1 : row DFTs of o'_j  (refined crop; pass C)
+//   XCORR_B: planes M, M + 1: the model intensity sum_p |Psi_p|^2 and the
+//            counts I_j (real images, unshifted; pass B), turned into row
+//            DFTs by xcorrb_rows
+// and the same correlation passes follow:
 // xcorr_cols : column DFTs of both planes -> A = F(o_j), B = F(o'_j);
 //              X = B conj(A) is stored in plane M; inverse column DFTs of X
 //              into plane M+1.
@@ -126,6 +130,43 @@ k_xcorr_cols(float2* __restrict__ scratch, int npl, int M, int CB,
     inv_stepB<W>(v, lane, lbuf);
 #pragma unroll
     for (int n1 = 0; n1 < G::N1; ++n1) colB[(size_t)(G::N2 * n1 + lane) * W] = v[n1];
+  }
+}
+
+// ------------------------------------------------------------ xcorrb_rows
+// XCORR_B: forward row DFTs of the two real images pass B left in planes M
+// (model intensity) and M + 1 (counts); the correlation passes then take
+// them exactly as they take the two crops' row DFTs for XCORR_A.  The two
+// planes are consecutive, so a CTA's RX lines are rows of a 2W-row block.
+template <int W>
+__global__ void __launch_bounds__(256)
+k_xcorrb_rows(float2* __restrict__ scratch, int npl, int M, int RX,
+              const float2* __restrict__ tw_g) {
+  using G = Line<W>;
+  extern __shared__ float4 smem4[];
+  float2* tw = reinterpret_cast<float2*>(smem4);
+  float2* tbuf = tw + W;
+  pdl_trigger();
+  for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
+  pdl_wait();  // both images come from the column pass
+  __syncthreads();
+  const int lp = blockIdx.y, r0 = blockIdx.x * RX;
+  const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
+  const bool act = line < RX;
+  float2* lbuf = tbuf + line * G::LP;
+  float2* row = scratch + (((size_t)lp * npl + M) * W + r0 + (act ? line : 0)) * W;
+  if (act && lane < G::N2) {
+    float2 v[G::N1];
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = row[G::N2 * n1 + lane];
+    fwd_step1<W>(v, lane, tw, lbuf);
+  }
+  __syncthreads();
+  if (act && lane < G::N1) {
+    float2 z[G::N2];
+    fwd_step3<W>(z, lane, lbuf);
+#pragma unroll
+    for (int k2 = 0; k2 < G::N2; ++k2) row[lane + G::N1 * k2] = z[k2];
   }
 }
 
@@ -433,6 +474,8 @@ cudaError_t set_refine_smem(const RefGeo& g) {
     if (e == cudaSuccess)
       e = allow_max_smem((const void*)k_xcorr_rows<WW>);
     if (e == cudaSuccess)
+      e = allow_max_smem((const void*)k_xcorrb_rows<WW>);
+    if (e == cudaSuccess)
       e = allow_max_smem((const void*)k_updft_part<WW>);
   });
   return e;
@@ -455,6 +498,19 @@ cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, 
     using G = Line<WW>;
     e = launch_pdl(k_xcorr_cols<WW>, dim3(WW / g.CBX, npatch), dim3(g.CBX * G::L), g.smX, s,
                    scratch, npl, M, g.CBX, tw);
+  });
+  return e;
+}
+
+cudaError_t launch_xcorrb_rows(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
+                               const float2* tw, cudaStream_t s) {
+  if (npatch <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  PTY_DISPATCH_W(g.W, {
+    using G = Line<WW>;
+    const int thr = (g.RX * G::L + 31) / 32 * 32;
+    e = launch_pdl(k_xcorrb_rows<WW>, dim3(2 * WW / g.RX, npatch), dim3(thr), g.smR, s, scratch,
+                   npl, M, g.RX, tw);
   });
   return e;
 }

@@ -37,9 +37,9 @@ k_cols(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
        float* __restrict__ err_part, int npl, int ppcb, int npatch,
-       const __grid_constant__ CUtensorMap tmap, int use_tma, int* err) {
+       const __grid_constant__ CUtensorMap tmap, int use_tma, int* err, int xb) {
   cols_body<W, CB, GRAD>(scratch, M, I, ids, tw_g, inv_w, eps, err_part, npl, ppcb, npatch,
-                         blockIdx.x, blockIdx.y, use_tma ? &tmap : nullptr, err);
+                         blockIdx.x, blockIdx.y, use_tma ? &tmap : nullptr, err, xb);
 }
 
 template <int W, bool PSTAGE>
@@ -501,7 +501,7 @@ cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx, cons
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
                         float eps, float* err_part, const CUtensorMap* tm, int* err,
-                        cudaStream_t s) {
+                        cudaStream_t s, int xb) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   cudaError_t e = cudaSuccess;
@@ -511,12 +511,12 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, eps, err_part,
                                                            t.npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err)
+                                                           tm ? *tm : none, tm ? 1 : 0, err, xb)
                                                     : launch_pdl(k_cols<WW, CBB, false, false>,
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, eps, err_part,
                                                            t.npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err)));
+                                                           tm ? *tm : none, tm ? 1 : 0, err, xb)));
   return e;
 }
 
@@ -533,12 +533,12 @@ cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, delta,
                                                            loss_part, npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err)
+                                                           tm ? *tm : none, tm ? 1 : 0, err, -1)
                                                     : launch_pdl(k_cols<WW, CBB, true, false>,
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, delta,
                                                            loss_part, npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err)));
+                                                           tm ? *tm : none, tm ? 1 : 0, err, -1)));
   return e;
 }
 
@@ -547,17 +547,19 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             float2* scratch, const float* omax_part,
                             const float* pmax_part, const float2* tw,
                             const UpdArgs& a, float2* pnum, float* pden,
-                            float* osum, int accumulate, int* err, cudaStream_t s) {
+                            float* osum, int accumulate, int* err, cudaStream_t s,
+                            int refine) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
   cudaError_t e = cudaSuccess;
+  const int rf = refine < 0 ? t.refine : (refine && t.refine);
   PTY_DISPATCH_W(t.W, e = t.pstage
       ? launch_pdl(k_rows_inv<WW, true>, grid, dim3(t.thrC), t.smC, s, O, Hx, P, t.M, t.R, t.ppc,
                    ids, corners, npatch, scratch, omax_part, pmax_part, t.n_pmax, tw, a, pnum,
-                   pden, osum, accumulate, t.npl, t.refine, err)
+                   pden, osum, accumulate, t.npl, rf, err)
       : launch_pdl(k_rows_inv<WW, false>, grid, dim3(t.thrC), t.smC, s, O, Hx, P, t.M, t.R,
                    t.ppc, ids, corners, npatch, scratch, omax_part, pmax_part, t.n_pmax, tw, a,
-                   pnum, pden, osum, accumulate, t.npl, t.refine, err));
+                   pnum, pden, osum, accumulate, t.npl, rf, err));
   return e;
 }
 

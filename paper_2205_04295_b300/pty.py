@@ -43,7 +43,8 @@ class RpieParams(ctypes.Structure):
 
 class RefineParams(ctypes.Structure):
     _fields_ = [("upsample", c_int), ("lr", c_float), ("b1", c_float), ("b2", c_float),
-                ("eps", c_float), ("start_iter", c_int), ("max_step", c_float)]
+                ("eps", c_float), ("start_iter", c_int), ("max_step", c_float),
+                ("point", c_int)]
 
 
 K_NAMES = ["rows_fwd", "cols", "rows_inv", "probe", "reduce", "refine", "grad", "other"]
@@ -74,8 +75,11 @@ def rpie_params(alpha_O=1.0, alpha_P=1.0, beta=1.0, gamma=0.1, eps=1.0, reg_eps=
     return RpieParams(alpha_O, alpha_P, beta, gamma, eps, reg_eps, max_group, int(update_probe))
 
 
-def refine_params(upsample=20, lr=0.5, b1=0.9, b2=0.999, eps=1e-8, start_iter=0, max_step=0.0):
-    return RefineParams(upsample, lr, b1, b2, eps, start_iter, max_step)
+def refine_params(upsample=20, lr=0.5, b1=0.9, b2=0.999, eps=1e-8, start_iter=0, max_step=0.0,
+                  point="A"):
+    """point: "A" (XCORR_A, object plane) or "B" (XCORR_B, detector plane)."""
+    return RefineParams(upsample, lr, b1, b2, eps, start_iter, max_step,
+                        {"A": 0, "B": 1}[point])
 
 
 _SIGS = {
