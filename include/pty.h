@@ -66,8 +66,12 @@ typedef struct {
   size_t scratch_bytes; /* cap on the far-field scratch; 0 = 64 MiB.  The
                            scratch holds M far-field waves per patch of a chunk
                            of one group; a smaller cap means smaller chunks. */
-  int flags;            /* reserved, 0 */
+  int flags;            /* PTY_FLAG_* bits, 0 = defaults */
 } pty_problem_desc;
+
+/* Take the registration's fine-grid matrix DFT on the FP32 cores instead of
+ * the tensor cores (3xTF32 tcgen05 MMAs, the default wherever K <= 32). */
+#define PTY_FLAG_FP32_REGISTRATION 1
 
 /* Update parameters of M-rPIE (M-rPIE section, Eqs. 5-7). */
 typedef struct {

@@ -235,6 +235,7 @@ struct pty_handle {
   pty_free_fn ff = nullptr;
   void* actx = nullptr;
   int device = 0;
+  int flags = 0;             // PTY_FLAG_* of the problem description
   pty::Tiling tl{}, tlr{};   // plain and refining launch geometry
   int Qc = 1, Qcr = 1, nslots = 1;
   pty::RefGeo rg{};
@@ -502,7 +503,7 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0) {
       CU(pty::launch_xcorr_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->cval, h->cidx,
                                 h->stream));
       CU(pty::launch_updft(h->rg, h->scratch, tl.npl, h->M, idc, nc, h->cval, h->cidx,
-                           h->roots, h->upart, h->shift, h->gap, h->stream));
+                           h->roots, h->upart, h->shift, h->gap, h->tma_err, h->stream));
       h->n_launch[PTY_K_REFINE] += 2;
     }
   }
@@ -724,11 +725,13 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
   if (d->Hy < d->W || d->Hx < d->W) return fail(PTY_EINVAL, "object %dx%d smaller than W", d->Hy, d->Hx);
   if ((d->alloc == nullptr) != (d->free == nullptr))
     return fail(PTY_EINVAL, "alloc and free must be given together");
+  if (d->flags & ~PTY_FLAG_FP32_REGISTRATION) return fail(PTY_EINVAL, "unknown flags 0x%x", d->flags);
   pty_handle* h = new (std::nothrow) pty_handle();
   if (!h) return fail(PTY_ENOMEM, "host allocation failed");
   h->W = d->W; h->M = d->M; h->N = d->N; h->Hy = d->Hy; h->Hx = d->Hx;
   h->stream = static_cast<cudaStream_t>(d->stream);
   h->af = d->alloc; h->ff = d->free; h->actx = d->alloc_ctx;
+  h->flags = d->flags;
   auto bail = [&](int rc) { delete h; return rc; };
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     cudaGetLastError();
@@ -967,7 +970,7 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
       (r->point != PTY_XCORR_A && r->point != PTY_XCORR_B))
     return fail(PTY_EINVAL, "bad refine parameters");
   if (r->upsample != h->roots_U) {
-    h->rg = pty::make_refgeo(h->W, r->upsample);
+    h->rg = pty::make_refgeo(h->W, r->upsample, !(h->flags & PTY_FLAG_FP32_REGISTRATION));
     if (h->rg.smU > 227 * 1024) return fail(PTY_EINVAL, "upsample %d too large for W=%d", r->upsample, h->W);
     CU(pty::set_refine_smem(h->rg));
     CU(pty::set_smem_limits(h->tlr));

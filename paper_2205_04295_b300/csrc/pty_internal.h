@@ -138,8 +138,10 @@ struct RefGeo {
   int CBX, RX;   // columns / rows per CTA of the correlation passes
   int RB;        // rows of X per CTA of the upsampled matrix DFT
   size_t smX, smR, smU;
+  bool tc;       // fine-grid DFT on the tensor cores (K <= 32 and not turned off)
 };
-RefGeo make_refgeo(int W, int U);
+// tc: take the tensor-core form of the fine-grid DFT where it applies (K <= 32)
+RefGeo make_refgeo(int W, int U, bool tc = true);
 cudaError_t set_refine_smem(const RefGeo& g);
 // roots exp(+2 pi i n / (U W)), n = 0..U W - 1 (host, double -> float)
 void make_up_roots(int W, int U, float2* out);
@@ -151,10 +153,11 @@ cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, 
 cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, int M,
                               int npatch, const float2* tw, float* cval, int* cidx,
                               cudaStream_t s);
-// part: npatch * (W / 16) * K * K complex partial sums of the fine grid
+// part: npatch * (W / 16) * K * K complex partial sums of the fine grid;
+// err: status word set by a tensor-core wait that gave up
 cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
                          int npatch, const float* cval, const int* cidx, const float2* roots,
-                         float2* part, float* shift, float* gap, cudaStream_t s);
+                         float2* part, float* shift, float* gap, int* err, cudaStream_t s);
 cudaError_t launch_adam(float* pos, float* m, float* v, const float* g, int N, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, float max_step,
                         float ymax, float xmax, cudaStream_t s);

@@ -29,6 +29,7 @@
 #include "pty_fft.cuh"
 #include "pty_internal.h"
 #include "pty_pdl.cuh"
+#include "pty_tc.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -332,6 +333,263 @@ k_updft_part(const float2* __restrict__ scratch, int npl, int M, int nparts,
   }
 }
 
+// ------------------------------------------------------------ updft_tc
+// Tensor-core form of updft_part (tcgen05, kind::tf32, 3xTF32 split): CTA
+// (tile of 128 rows of X, patch).  T = X_rows E_c is taken on the
+// 5th-generation tensor cores as one real GEMM pair into a 128 x 64 FP32
+// accumulator in TMEM (columns 0-31 Re T, 32-63 Im T):
+//   [Re T | Im T] = Xr [Ecr | Eci] + Xi [-Eci | Ecr]   (M 128, N 64, K = W).
+// Every operand is split x = hi + lo into TF32 parts and each product is
+// hi hi + hi lo + lo hi, which keeps about 21 bits of each operand
+// (FP32-level results).  X is staged by cp.async one chunk of 32 columns
+// ahead, split into four K-major planes (Xr hi, Xr lo, Xi hi, Xi lo) and the
+// matching chunk of the two E_c operands (rows = [k | 32 + k], zero for
+// k >= K) into four more; one thread issues the chunk's 24 MMAs (M 128,
+// N 64, K 8) and commits them to an mbarrier (bounded wait).  The phases
+// exp(2 pi i n / (U W)) come from the root table, staged into shared memory
+// before the dependency wait; their indices are stepped in 32-bit integers.
+// The block's share E_r[:, rows] T (K x K) is then taken on the FP32 cores
+// (2 x 2 outputs per thread) from T copied to shared memory, and updft_final
+// adds the shares.  Rows past W (W < 128, or the second tile at W = 192)
+// are zero.
+constexpr int kTcRows = 128;                  // M of the MMA: rows of X per CTA
+constexpr int kTcKc = 32;                     // columns of X (index v) per chunk
+constexpr int kTcN = 32;                      // fine-grid points held (K <= 32)
+constexpr int kTcRawPitch = kTcKc + 2;        // complex per staged row (272 B)
+constexpr int kTcTPitch = kTcN + 1;           // complex per row of T in shared memory
+constexpr int kTcAPlane = kTcRows * kTcKc * 4;    // bytes of one A plane (128 x 32)
+constexpr int kTcBPlane = 2 * kTcN * kTcKc * 4;   // bytes of one B plane (64 x 32)
+constexpr int kTcSBO = (kTcKc / 4) * 128;         // bytes between 8-row groups
+constexpr int kTcRaw = 2 * kTcRows * kTcRawPitch * 8;
+constexpr int kTcFixed = kTcRaw + 4 * kTcAPlane + 4 * kTcBPlane + 128;  // + the root table
+static_assert(kTcRows * kTcTPitch * 8 <= kTcRaw, "T reuses the staging buffers");
+static_assert(kTcN * kTcRows * 8 <= 4 * kTcAPlane, "E_r reuses the A planes");
+
+// Byte offset of element (row, k) in a K-major, no-swizzle plane of kTcKc
+// columns: core matrices (8 rows x 4 values, 128 bytes) with the K-adjacent
+// ones contiguous (LBO = 128) and the row-adjacent ones kTcKc / 4 apart
+// (SBO = kTcSBO).
+__device__ __forceinline__ int tc_off(int row, int k) {
+  return ((row >> 3) * (kTcKc / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+__device__ __forceinline__ int modp32(int a, int m) {
+  const int r = a % m;
+  return r < 0 ? r + m : r;
+}
+__device__ __forceinline__ void split4(const float* x, float4& hi, float4& lo) {
+  tf32_split(x[0], hi.x, lo.x);
+  tf32_split(x[1], hi.y, lo.y);
+  tf32_split(x[2], hi.z, lo.z);
+  tf32_split(x[3], hi.w, lo.w);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 1)
+k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
+           const float* __restrict__ cval, const int* __restrict__ cidx,
+           const float2* __restrict__ roots_g, int U, int K, float2* __restrict__ part,
+           int* __restrict__ err) {
+  extern __shared__ float4 smem4[];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tslot;
+  __shared__ float rv[32];
+  __shared__ int ri[32];
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem4) + 127) &
+                                       ~static_cast<uintptr_t>(127));
+  float2* raw = reinterpret_cast<float2*>(base);   // 2 x [128][kTcRawPitch]
+  char* Ap = base + kTcRaw;                         // Xr hi, Xr lo, Xi hi, Xi lo
+  char* Bp = Ap + 4 * kTcAPlane;                    // B1 hi, B1 lo, B2 hi, B2 lo
+  float2* roots = reinterpret_cast<float2*>(Bp + 4 * kTcBPlane);  // U W roots
+  float2* T = raw;                                  // [128][kTcTPitch] after the MMAs
+  float2* Er = reinterpret_cast<float2*>(Ap);       // [K][128] after the MMAs
+
+  const int lp = blockIdx.y, u0 = blockIdx.x * kTcRows;
+  const int nrows = min(kTcRows, W - u0);
+  const int UW = U * W, half = K / 2;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const float2* X = scratch + ((size_t)lp * npl + M) * W * W + (size_t)u0 * W;
+  constexpr int nch = W / kTcKc;
+  constexpr unsigned long long kLimit = 200000000ull;  // 0.2 s of the global timer
+  pdl_trigger();
+  if (warp == 0) tmem_alloc(&tslot, 64);
+  if (tid == 0) mbar_init(&mbar, 1);
+  // the root table does not depend on earlier kernels: staged before the wait
+  for (int i = tid; i < UW / 2; i += blockDim.x) cp_async<16>(roots + 2 * i, roots_g + 2 * i);
+  cp_async_commit();
+  // rows past W stay zero in both staging buffers
+  const int zr = (kTcRows - nrows) * kTcRawPitch;
+  for (int i = tid; i < 2 * zr; i += blockDim.x)
+    raw[(i / zr) * kTcRows * kTcRawPitch + nrows * kTcRawPitch + i % zr] = make_float2(0.f, 0.f);
+  pdl_wait();  // X and the coarse peaks come from the correlation passes
+  auto stage = [&](int c, int b) {
+    float2* dst = raw + b * kTcRows * kTcRawPitch;
+    for (int i = tid; i < nrows * (kTcKc / 2); i += blockDim.x) {
+      const int r = i / (kTcKc / 2), h = i - r * (kTcKc / 2);
+      cp_async<16>(dst + r * kTcRawPitch + 2 * h, X + (size_t)r * W + c * kTcKc + 2 * h);
+    }
+  };
+  stage(0, 0);
+  cp_async_commit();
+  int sy, sx;
+  coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);  // contains barriers
+  tc_fence_after_sync();
+  const uint32_t tm = tslot;
+  // E_c entry (v, k) = root[(v_s a_k) mod UW], a_k = U s_x + k - K/2; this
+  // thread's operand rows: fine-grid point kq = tid / 8, columns 4 (tid % 8) + 0..3
+  const int kq = tid >> 3, vq = 4 * (tid & 7);
+  const int a_k = modp32(U * sx + kq - half, UW);
+  const uint32_t idesc = tc_idesc_tf32(kTcRows, 2 * kTcN, false);
+  uint64_t da[4][kTcKc / 8], db[4][kTcKc / 8];  // descriptors: plane x K step
+  if (tid == 0) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int s = 0; s < kTcKc / 8; ++s) {
+        da[p][s] = tc_smem_desc(Ap + p * kTcAPlane + s * 256, 128, kTcSBO);
+        db[p][s] = tc_smem_desc(Bp + p * kTcBPlane + s * 256, 128, kTcSBO);
+      }
+  }
+  unsigned phase = 0;
+  for (int c = 0; c < nch; ++c) {
+    cp_async_wait<0>();
+    __syncthreads();  // chunk c (and the roots) have landed; the split of chunk c - 1 is done
+    if (c + 1 < nch) stage(c + 1, (c + 1) & 1);
+    cp_async_commit();
+    bool ok = true;
+    if (c > 0) {  // the MMAs of chunk c - 1 still read the planes
+      ok = mbar_wait_bounded(&mbar, phase, kLimit);
+      phase ^= 1;
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      if (!ok) mbar_wait_bounded(&mbar, phase ^ 1, kLimit);  // the MMAs in flight
+      cp_async_wait<0>();
+      tc_fence_before_sync();
+      __syncthreads();
+      if (warp == 0) tmem_dealloc(tm, 64);
+      return;
+    }
+    {  // X split: thread -> row m, core-matrix columns q = 4 (tid / 128) + 0..3
+      const int m = tid & (kTcRows - 1);
+      const float2* src = raw + (c & 1) * kTcRows * kTcRawPitch + m * kTcRawPitch;
+#pragma unroll
+      for (int qq = 0; qq < kTcKc / 8; ++qq) {
+        const int q = (kTcKc / 8) * (tid >> 7) + qq;
+        const float4 a = *reinterpret_cast<const float4*>(src + 4 * q);
+        const float4 b = *reinterpret_cast<const float4*>(src + 4 * q + 2);
+        const float re[4] = {a.x, a.z, b.x, b.z}, im[4] = {a.y, a.w, b.y, b.w};
+        float4 rh, rl, ih, il;
+        split4(re, rh, rl);
+        split4(im, ih, il);
+        const int off = tc_off(m, 4 * q);
+        *reinterpret_cast<float4*>(Ap + off) = rh;
+        *reinterpret_cast<float4*>(Ap + kTcAPlane + off) = rl;
+        *reinterpret_cast<float4*>(Ap + 2 * kTcAPlane + off) = ih;
+        *reinterpret_cast<float4*>(Ap + 3 * kTcAPlane + off) = il;
+      }
+    }
+    {  // E_c split: B1 = [Ecr | Eci], B2 = [-Eci | Ecr] (rows k and 32 + k)
+      float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f}, nci[4];
+      if (kq < K) {
+        const int v0 = c * kTcKc + vq;  // 4 | W / 2: the four columns share a sign
+        int n = modp32((v0 < W / 2 ? v0 : v0 - W) * a_k, UW);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 w = roots[n];
+          cr[e] = w.x;
+          ci[e] = w.y;
+          n += a_k;
+          if (n >= UW) n -= UW;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) nci[e] = -ci[e];
+      float4 rh, rl, ih, il, nh, nl;
+      split4(cr, rh, rl);
+      split4(ci, ih, il);
+      split4(nci, nh, nl);
+      const int o1 = tc_off(kq, vq), o2 = tc_off(kTcN + kq, vq);
+      *reinterpret_cast<float4*>(Bp + o1) = rh;
+      *reinterpret_cast<float4*>(Bp + kTcBPlane + o1) = rl;
+      *reinterpret_cast<float4*>(Bp + o2) = ih;
+      *reinterpret_cast<float4*>(Bp + kTcBPlane + o2) = il;
+      *reinterpret_cast<float4*>(Bp + 2 * kTcBPlane + o1) = nh;
+      *reinterpret_cast<float4*>(Bp + 3 * kTcBPlane + o1) = nl;
+      *reinterpret_cast<float4*>(Bp + 2 * kTcBPlane + o2) = rh;
+      *reinterpret_cast<float4*>(Bp + 3 * kTcBPlane + o2) = rl;
+    }
+    fence_proxy_async();  // the planes, written through the generic proxy, go to the MMA
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after_sync();
+#pragma unroll
+      for (int s = 0; s < kTcKc / 8; ++s) {
+        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+        tc_mma_tf32(tm, da[0][s], db[0][s], idesc, acc);  // Xr hi B1 hi
+        tc_mma_tf32(tm, da[0][s], db[1][s], idesc, 1u);   // Xr hi B1 lo
+        tc_mma_tf32(tm, da[1][s], db[0][s], idesc, 1u);   // Xr lo B1 hi
+        tc_mma_tf32(tm, da[2][s], db[2][s], idesc, 1u);   // Xi hi B2 hi
+        tc_mma_tf32(tm, da[2][s], db[3][s], idesc, 1u);   // Xi hi B2 lo
+        tc_mma_tf32(tm, da[3][s], db[2][s], idesc, 1u);   // Xi lo B2 hi
+      }
+      tc_commit(&mbar);
+    }
+  }
+  const bool ok = mbar_wait_bounded(&mbar, phase, kLimit);  // the last chunk's MMAs
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(err, 1);
+    if (!ok) mbar_wait_bounded(&mbar, phase, kLimit);
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tm, 64);
+    return;
+  }
+  tc_fence_after_sync();
+  {  // T -> shared memory: warps 0-3 Re T, 4-7 Im T of row 32 (warp % 4) + lane
+    float v[kTcN];
+    tmem_ld32(tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kTcN), v);
+    const int m = 32 * (warp & 3) + (tid & 31);
+    float* Tf = reinterpret_cast<float*>(T) + 2 * m * kTcTPitch + (warp >> 2);
+#pragma unroll
+    for (int k = 0; k < kTcN; ++k) Tf[2 * k] = v[k];
+  }
+  // this block's E_r columns: Er[k1][r] = root[(u_s (U s_y + k1 - K/2)) mod UW]
+  for (int t = tid; t < K * kTcRows; t += blockDim.x) {
+    const int k1 = t / kTcRows, r = t - k1 * kTcRows, u = u0 + r;
+    const int b = modp32(U * sy + k1 - half, UW);
+    Er[t] = r < nrows ? roots[modp32((u < W / 2 ? u : u - W) * b, UW)] : make_float2(0.f, 0.f);
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after_sync();
+    tmem_dealloc(tm, 64);
+  }
+  // share of this row block: sum_r E_r[k1][u0 + r] T[r][k2], 2 x 2 outputs per thread
+  float2* dst = part + ((size_t)lp * gridDim.x + blockIdx.x) * K * K;
+  const int nb = (K + 1) / 2;
+  if (tid < nb * nb) {
+    const int k1 = 2 * (tid / nb), k2 = 2 * (tid % nb);
+    const bool y1 = k1 + 1 < K, x1 = k2 + 1 < K;
+    const float2* e0 = Er + k1 * kTcRows;
+    const float2* e1 = Er + (y1 ? k1 + 1 : k1) * kTcRows;
+    float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;
+#pragma unroll 4
+    for (int r = 0; r < nrows; ++r) {
+      const float2 a0 = e0[r], a1 = e1[r];
+      const float2 t0 = T[r * kTcTPitch + k2], t1 = T[r * kTcTPitch + k2 + 1];
+      cfma(c00, a0, t0);
+      cfma(c01, a0, t1);
+      cfma(c10, a1, t0);
+      cfma(c11, a1, t1);
+    }
+    dst[k1 * K + k2] = c00;
+    if (x1) dst[k1 * K + k2 + 1] = c01;
+    if (y1) dst[(k1 + 1) * K + k2] = c10;
+    if (y1 && x1) dst[(k1 + 1) * K + k2 + 1] = c11;
+  }
+}
+
 __global__ void __launch_bounds__(256)
 k_updft_final(const int* __restrict__ ids, int W, int nblocks, int nparts,
               const float* __restrict__ cval, const int* __restrict__ cidx, int U, int K,
@@ -445,11 +703,13 @@ template <int W> static void refgeo_fill(RefGeo& g) {
   g.smR = (size_t)(W + g.RX * G::LP) * sizeof(float2);
 }
 
-RefGeo make_refgeo(int W, int U) {
+RefGeo make_refgeo(int W, int U, bool tc) {
   RefGeo g{};
   g.W = W;
   g.U = std::max(1, U);
   g.K = (int)std::ceil(1.5 * g.U);
+  g.tc = tc && g.U > 1 && g.K <= kTcN &&
+         (size_t)kTcFixed + (size_t)g.U * W * sizeof(float2) <= (size_t)smem_optin() - 1024;
   switch (W) {
     case 32: refgeo_fill<32>(g); break;
     case 64: refgeo_fill<64>(g); break;
@@ -477,6 +737,8 @@ cudaError_t set_refine_smem(const RefGeo& g) {
       e = allow_max_smem((const void*)k_xcorrb_rows<WW>);
     if (e == cudaSuccess)
       e = allow_max_smem((const void*)k_updft_part<WW>);
+    if (e == cudaSuccess)
+      e = allow_max_smem((const void*)k_updft_tc<WW>);
   });
   return e;
 }
@@ -531,18 +793,25 @@ cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, i
 
 cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
                          int npatch, const float* cval, const int* cidx, const float2* roots,
-                         float2* part, float* shift, float* gap, cudaStream_t s) {
+                         float2* part, float* shift, float* gap, int* err, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   const int nparts = g.W / g.RX;
   if (g.U <= 1) {
     k_coarse_only<<<npatch, 128, 0, s>>>(ids, nparts, g.W, cval, cidx, shift, gap);
     return cudaGetLastError();
   }
-  const int nblocks = g.W / g.RB;
+  const int nblocks = g.tc ? (g.W + kTcRows - 1) / kTcRows : g.W / g.RB;
   cudaError_t e = cudaSuccess;
-  PTY_DISPATCH_W(g.W, e = launch_pdl(k_updft_part<WW>, dim3(nblocks, npatch), dim3(512), g.smU,
-                                     s, scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K,
-                                     g.RB, part));
+  if (g.tc) {
+    const size_t sm = (size_t)kTcFixed + (size_t)g.U * g.W * sizeof(float2);
+    PTY_DISPATCH_W(g.W, e = launch_pdl(k_updft_tc<WW>, dim3(nblocks, npatch), dim3(256), sm, s,
+                                       scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K,
+                                       part, err));
+  } else {
+    PTY_DISPATCH_W(g.W, e = launch_pdl(k_updft_part<WW>, dim3(nblocks, npatch), dim3(512), g.smU,
+                                       s, scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K,
+                                       g.RB, part));
+  }
   if (e != cudaSuccess) return e;
   return launch_pdl(k_updft_final, dim3(npatch), dim3(256), 0, s, ids, g.W, nblocks, nparts,
                     cval, cidx, g.U, g.K, part, shift, gap);

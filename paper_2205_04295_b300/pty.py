@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libpty.so")
 
 PTY_OK, PTY_EINVAL, PTY_ENOMEM, PTY_ECUDA, PTY_EDATA, PTY_ETIMEOUT, PTY_ESTATE = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
+FLAG_FP32_REGISTRATION = 1
 ERR_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EDATA", 5: "ETIMEOUT", 6: "ESTATE"}
 
 c_int, c_float, c_void_p, c_size_t = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
@@ -291,9 +292,12 @@ class Problem:
     """One reconstruction problem (a pty_handle) on the current CUDA device.
 
     Device memory comes from PyTorch's caching allocator by default
-    (``allocator="torch"``); ``"cuda"`` lets the library call cudaMalloc."""
+    (``allocator="torch"``); ``"cuda"`` lets the library call cudaMalloc.
+    ``fp32_registration`` takes the registration's fine-grid DFT on the FP32
+    cores instead of the tensor cores."""
 
-    def __init__(self, W, M, N, Hy, Hx, stream=None, scratch_bytes=0, allocator="torch"):
+    def __init__(self, W, M, N, Hy, Hx, stream=None, scratch_bytes=0, allocator="torch",
+                 fp32_registration=False):
         import torch
         self.W, self.M, self.N, self.Hy, self.Hx = W, M, N, Hy, Hx
         if stream is None:
@@ -301,7 +305,7 @@ class Problem:
         self.stream = stream
         af, ff, self._allocator = _hooks(allocator)
         d = ProblemDesc(W, M, N, Hy, Hx, c_void_p(stream.cuda_stream), af, ff,
-                        None, scratch_bytes, 0)
+                        None, scratch_bytes, FLAG_FP32_REGISTRATION if fp32_registration else 0)
         h = c_void_p()
         check(lib().pty_init_problem(ctypes.byref(d), ctypes.byref(h)))
         self.h = h

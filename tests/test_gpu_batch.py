@@ -53,6 +53,24 @@ def test_batch_equals_standalone_runs_and_oracle():
     b.close()
 
 
+def test_batch_50_iterations_against_the_oracle():
+    """All six problems of the uneven mix, 50 M-rPIE iterations in one
+    persistent launch (the batched workload's iteration count), against the
+    FP64 oracle run problem by problem: relative L2 <= 1e-3 (the bar for long
+    runs) on object and probe, and the error curve to 1e-3."""
+    wls = small_mix()
+    ds = [build(w) for w in wls]
+    b = run_batch(wls, ds, 50)
+    b.run(50)
+    assert list(b.status()) == [0] * len(wls)
+    for k, (w, d) in enumerate(zip(wls, ds)):
+        st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+        rpie.run(st, d["I"], rpie.RPIEParams(), 50)
+        assert rel_l2(b.problems[k].object(False), st.O) <= 1e-3, k
+        assert rel_l2(b.problems[k].probe(False), st.P) <= 1e-3, k
+    b.close()
+
+
 def test_schedule_variants_give_identical_results():
     wls = small_mix()[:4]
     ds = [build(w) for w in wls]

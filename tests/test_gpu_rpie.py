@@ -37,9 +37,11 @@ def check_one_iteration(wl, d, scratch_bytes=0, **kw):
     Og, Pg = prob.object(False), prob.probe(False)
     assert rel_l2(Og, st.O) <= TOL1
     assert rel_l2(Pg, st.P) <= TOL1
-    # the changes themselves (the unscanned object stays 1 and dilutes the above)
-    assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= 2e-4
-    assert rel_l2(Pg - d["P0"], st.P - d["P0"]) <= 2e-4
+    # the changes themselves, to the same bar (the unscanned object stays 1
+    # and would dilute the whole-array figures): measured 3e-7 to 6e-7 for
+    # every case of this file on a B300
+    assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= TOL1
+    assert rel_l2(Pg - d["P0"], st.P - d["P0"]) <= TOL1
     Ig = prob.model_intensities(False)
     Io = model.model_intensities(st.O, st.P, d["pos"])
     assert rel_l2(Ig, Io) <= TOL1
@@ -291,9 +293,9 @@ def sampled_groups_parity(wl, n_groups):
     assert abs(eg - err / total) <= TOL1 * (err / total)
     Og = prob.object(False)
     assert rel_l2(Og, st.O) <= TOL1
-    assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= 2e-4
+    assert rel_l2(Og - d["O0"], st.O - d["O0"]) <= TOL1
     assert rel_l2(prob.probe(False), st.P) <= TOL1
-    assert rel_l2(prob.probe(False) - d["P0"], st.P - d["P0"]) <= 2e-4
+    assert rel_l2(prob.probe(False) - d["P0"], st.P - d["P0"]) <= TOL1
     prob.close()
 
 
