@@ -420,6 +420,7 @@ int check_params(const pty_rpie_params* p) {
   for (float x : v)
     if (!std::isfinite(x)) return fail(PTY_EINVAL, "non-finite rpie parameter");
   if (p->max_group < 0) return fail(PTY_EINVAL, "max_group < 0");
+  if (p->eps < 0.f) return fail(PTY_EINVAL, "eps < 0");
   return PTY_OK;
 }
 

@@ -201,6 +201,7 @@ template <int W> struct Line {
 template <int W>
 PTY_D void fwd_step1(float2* v, int lane, const float2* tw, float2* buf) {
   using G = Line<W>;
+  __builtin_assume(lane >= 0 && lane < G::N2);  // lets the padded offsets fold to constants
   Dft<G::N1, false>::run(v);
 #pragma unroll
   for (int k1 = 0; k1 < G::N1; ++k1) {
@@ -213,6 +214,7 @@ PTY_D void fwd_step1(float2* v, int lane, const float2* tw, float2* buf) {
 template <int W>
 PTY_D void fwd_step3(float2* z, int lane, const float2* buf) {
   using G = Line<W>;
+  __builtin_assume(lane >= 0 && lane < G::N1);
 #pragma unroll
   for (int n2 = 0; n2 < G::N2; ++n2) z[n2] = buf[G::sp(G::N2 * lane + n2)];
   Dft<G::N2, false>::run(z);
@@ -222,6 +224,7 @@ PTY_D void fwd_step3(float2* z, int lane, const float2* buf) {
 template <int W>
 PTY_D void inv_stepA(float2* z, int lane, const float2* tw, float2* buf) {
   using G = Line<W>;
+  __builtin_assume(lane >= 0 && lane < G::N1);
   Dft<G::N2, true>::run(z);
 #pragma unroll
   for (int n2 = 0; n2 < G::N2; ++n2) {
@@ -234,6 +237,7 @@ PTY_D void inv_stepA(float2* z, int lane, const float2* tw, float2* buf) {
 template <int W>
 PTY_D void inv_stepB(float2* v, int lane, const float2* buf) {
   using G = Line<W>;
+  __builtin_assume(lane >= 0 && lane < G::N2);
 #pragma unroll
   for (int k1 = 0; k1 < G::N1; ++k1) v[k1] = buf[G::sp(G::N2 * k1 + lane)];
   Dft<G::N1, true>::run(v);

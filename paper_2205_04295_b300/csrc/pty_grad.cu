@@ -164,8 +164,11 @@ k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__
 }
 
 // ---------------------------------------------------- inverse rows + adjoint
-// The object rows of the next patch are requested while the current patch
-// is transformed (the far-field rows are read straight into registers).
+// The far-field rows and the object rows of the next patch are requested
+// (cp.async) while the current patch is transformed, so no register waits on
+// a global load; the probe values are read at use through L1 (the CTA's
+// rows of P, a few KB, stay cached), which leaves their shared memory to the
+// far-field stage.
 template <int W>
 __global__ void __launch_bounds__(256)
 k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__ P, int M,
@@ -178,8 +181,8 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
   extern __shared__ float4 smem4[];
   const int TB = max(M * R * G::LP, M * R * W);
   float2* tw = reinterpret_cast<float2*>(smem4);
-  float2* Prow = tw + W;
-  float2* tbuf = Prow + M * R * W;  // transpose buffer, then conj(P) G_psi terms
+  float2* zst = tw + W;             // M x R x W far-field rows of the patch
+  float2* tbuf = zst + M * R * W;   // transpose buffer, then conj(P) G_psi terms
   float2* gp = tbuf + TB;           // dL/dP partial sums of this CTA
   float2* obuf = gp + M * R * W;    // R x W interpolated crop rows
   float2* st = obuf + R * W;        // 2 x (R + 1) x (W + 1) object rows
@@ -195,15 +198,21 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
     sb[t] = bil_of(pos, sj[t]);
   }
   __syncthreads();
-  auto stage = [&](int q, float2* stq) { grad_stage<W>(O, Hx, sb[q - p0], R, r0, stq); };
+  // patch q's object rows into stq and its far-field rows (16-byte pieces) into zst
+  auto stage = [&](int q, float2* stq) {
+    grad_stage<W>(O, Hx, sb[q - p0], R, r0, stq);
+    constexpr int hw = W / 2;
+    for (int i = threadIdx.x; i < M * R * hw; i += blockDim.x) {
+      const int line = i / hw, h = i - line * hw;  // line = mode * R + row
+      const int kk = line / R, rr = line - kk * R;
+      cp_async<16>(zst + line * W + 2 * h,
+                   scratch + (((size_t)q * npl + kk) * W + r0 + rr) * W + 2 * h);
+    }
+  };
   if (p0 < p1) stage(p0, st);
   cp_async_commit();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
-  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
-    const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
-    Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
-    gp[e] = make_float2(0.f, 0.f);
-  }
+  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) gp[e] = make_float2(0.f, 0.f);
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
   const bool act = line < M * R;
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
@@ -213,9 +222,9 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
     const Bil b = sb[lp - p0];
     const float2* sc = st + ((lp - p0) & 1) * (R + 1) * SP;
     cp_async_wait<0>();
-    __syncthreads();  // this patch's rows have landed
+    __syncthreads();  // this patch's object and far-field rows have landed
     if (act && lane < G::N1) {
-      const float2* src = scratch + (((size_t)lp * npl + k) * W + r0 + r) * W;
+      const float2* src = zst + (k * R + r) * W;
       float2 z[G::N2];
 #pragma unroll
       for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = src[lane + G::N1 * k2];
@@ -225,7 +234,7 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
       const int rr = e / W, c = e - rr * W;
       bil_staged<W>(sc, b, rr, c, obuf[e]);
     }
-    __syncthreads();  // request the next patch's object rows
+    __syncthreads();  // the stage is read: request the next patch's rows
     if (lp + 1 < p1) stage(lp + 1, st + ((lp + 1 - p0) & 1) * (R + 1) * SP);
     cp_async_commit();
     float2 v[G::N1];
@@ -236,7 +245,7 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
         const float2 o = obuf[r * W + c];
-        const float2 Pk = Prow[(k * R + r) * W + c];
+        const float2 Pk = __ldg(P + ((size_t)k * W + r0 + r) * W + c);
         gp[(k * R + r) * W + c] = cadd(gp[(k * R + r) * W + c], cmulc(v[n1], o));  // conj(o) G_psi
         tbuf[(k * R + r) * W + c] = cmulc(v[n1], Pk);                              // conj(P) G_psi
       }

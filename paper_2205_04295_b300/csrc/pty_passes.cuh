@@ -338,13 +338,15 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
       for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
         const int u = el / CB, cl = el - u * CB;
         float s = 0.f;
+#pragma unroll 4
         for (int kk = 0; kk < M; ++kk) s += Sb[(kk * W + u) * CB + cl];
         const float sI = sqrtf((float)cn[el]);
         if (!GRAD) {
           const float a = sqrtf(s) * inv_w;
           const float d = a - sI;
           e = fmaf(d, d, e);
-          Sb[u * CB + cl] = sI / (a + eps) * f2;
+          // quotient by a reciprocal-multiply (within 2 ulp of the division)
+          Sb[u * CB + cl] = __fdividef(sI, a + eps) * f2;
           if (xb >= 0) {
             // XCORR_B: the model intensity and the counts, unshifted, as the
             // real parts of scratch planes xb and xb + 1
@@ -356,7 +358,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
           const float a = sqrtf(fmaf(s, f2, eps));
           const float d = a - sI;
           e = fmaf(d, d, e);
-          Sb[u * CB + cl] = 2.f * (1.f - sI / a) * f2;
+          Sb[u * CB + cl] = 2.f * (1.f - __fdividef(sI, a)) * f2;
         }
       }
     }

@@ -80,14 +80,17 @@ def test_sequential_mode_and_fixed_probe():
     check_one_iteration(wl, d, update_probe=False)
 
 
-def test_plain_rpie_20_iterations():
+def test_plain_rpie_100_iterations():
+    """64x64 / 1 mode / 10x10 raster, 100 free iterations (the workload's 20
+    and then 80 more): the bar for long runs is 1e-3; measured on a B300:
+    object 1.2e-6, probe 9.4e-7, error curve 4.3e-7."""
     wl = synth.plain_rpie_64()
     d = build(wl)
     pg, po = params_pair()
     prob = gpu_problem(wl, d)
-    eg = prob.run(wl.n_iter, pg)
+    eg = prob.run(100, pg)
     st = rpie.State.create(d["O0"], d["P0"], d["pos"])
-    eo = rpie.run(st, d["I"], po, wl.n_iter)
+    eo = rpie.run(st, d["I"], po, 100)
     assert rel_l2(prob.object(False), st.O) <= 1e-3
     assert rel_l2(prob.probe(False), st.P) <= 1e-3
     np.testing.assert_allclose(eg, eo, rtol=1e-3)
