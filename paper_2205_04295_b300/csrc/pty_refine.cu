@@ -336,32 +336,34 @@ k_updft_part(const float2* __restrict__ scratch, int npl, int M, int nparts,
 // ------------------------------------------------------------ updft_tc
 // Tensor-core form of updft_part (tcgen05, kind::tf32, 3xTF32 split): CTA
 // (tile of 128 rows of X, patch).  T = X_rows E_c is taken on the
-// 5th-generation tensor cores as one real GEMM pair into a 128 x 64 FP32
-// accumulator in TMEM (columns 0-31 Re T, 32-63 Im T):
+// 5th-generation tensor cores as one real GEMM pair,
 //   [Re T | Im T] = Xr [Ecr | Eci] + Xi [-Eci | Ecr]   (M 128, N 64, K = W).
 // Every operand is split x = hi + lo into TF32 parts and each product is
 // hi hi + hi lo + lo hi, which keeps about 21 bits of each operand
-// (FP32-level results).  X is staged by cp.async one chunk of 32 columns
-// ahead, split into four K-major planes (Xr hi, Xr lo, Xi hi, Xi lo) and the
-// matching chunk of the two E_c operands (rows = [k | 32 + k], zero for
-// k >= K) into four more; one thread issues the chunk's 24 MMAs (M 128,
-// N 64, K 8) and commits them to an mbarrier (bounded wait).  The phases
-// exp(2 pi i n / (U W)) come from the root table, staged into shared memory
-// before the dependency wait; their indices are stepped in 32-bit integers.
-// The block's share E_r[:, rows] T (K x K) is then taken on the FP32 cores
-// (2 x 2 outputs per thread) from T copied to shared memory, and updft_final
-// adds the shares.  Rows past W (W < 128, or the second tile at W = 192)
-// are zero.
+// (FP32-level results).  The hi and lo parts of an E_c operand are stacked
+// along N (rows 0-63 hi, 64-127 lo), so per K step one N = 128 MMA takes
+// X_hi [B_hi | B_lo] and one N = 64 MMA adds X_lo B_hi into the first half:
+// the 128 x 128 FP32 accumulator in TMEM holds [hi-hi + lo-hi | hi-lo]
+// products, added at read-out.  X is staged by cp.async one chunk of 32
+// columns ahead and split into four K-major planes (Xr hi, Xr lo, Xi hi,
+// Xi lo), the matching chunk of the two stacked E_c operands into two more;
+// one thread issues the chunk's 16 MMAs and commits them to an mbarrier
+// (bounded wait).  The phases exp(2 pi i n / (U W)) come from the root
+// table, staged into shared memory before the dependency wait; their indices
+// are stepped in 32-bit integers.  The block's share E_r[:, rows] T (K x K)
+// is then taken on the FP32 cores (2 x 2 outputs per thread) from T copied
+// to shared memory, and updft_final adds the shares.  Rows past W (W < 128,
+// or the second tile at W = 192) are zero.
 constexpr int kTcRows = 128;                  // M of the MMA: rows of X per CTA
 constexpr int kTcKc = 32;                     // columns of X (index v) per chunk
 constexpr int kTcN = 32;                      // fine-grid points held (K <= 32)
 constexpr int kTcRawPitch = kTcKc + 2;        // complex per staged row (272 B)
 constexpr int kTcTPitch = kTcN + 1;           // complex per row of T in shared memory
 constexpr int kTcAPlane = kTcRows * kTcKc * 4;    // bytes of one A plane (128 x 32)
-constexpr int kTcBPlane = 2 * kTcN * kTcKc * 4;   // bytes of one B plane (64 x 32)
+constexpr int kTcBPlane = 4 * kTcN * kTcKc * 4;   // bytes of one stacked B plane (128 x 32)
 constexpr int kTcSBO = (kTcKc / 4) * 128;         // bytes between 8-row groups
 constexpr int kTcRaw = 2 * kTcRows * kTcRawPitch * 8;
-constexpr int kTcFixed = kTcRaw + 4 * kTcAPlane + 4 * kTcBPlane + 128;  // + the root table
+constexpr int kTcFixed = kTcRaw + 4 * kTcAPlane + 2 * kTcBPlane + 128;  // + the root table
 static_assert(kTcRows * kTcTPitch * 8 <= kTcRaw, "T reuses the staging buffers");
 static_assert(kTcN * kTcRows * 8 <= 4 * kTcAPlane, "E_r reuses the A planes");
 
@@ -398,8 +400,8 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
                                        ~static_cast<uintptr_t>(127));
   float2* raw = reinterpret_cast<float2*>(base);   // 2 x [128][kTcRawPitch]
   char* Ap = base + kTcRaw;                         // Xr hi, Xr lo, Xi hi, Xi lo
-  char* Bp = Ap + 4 * kTcAPlane;                    // B1 hi, B1 lo, B2 hi, B2 lo
-  float2* roots = reinterpret_cast<float2*>(Bp + 4 * kTcBPlane);  // U W roots
+  char* Bp = Ap + 4 * kTcAPlane;                    // [B1 hi; B1 lo], [B2 hi; B2 lo]
+  float2* roots = reinterpret_cast<float2*>(Bp + 2 * kTcBPlane);  // U W roots
   float2* T = raw;                                  // [128][kTcTPitch] after the MMAs
   float2* Er = reinterpret_cast<float2*>(Ap);       // [K][128] after the MMAs
 
@@ -411,7 +413,7 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   constexpr int nch = W / kTcKc;
   constexpr unsigned long long kLimit = 200000000ull;  // 0.2 s of the global timer
   pdl_trigger();
-  if (warp == 0) tmem_alloc(&tslot, 64);
+  if (warp == 0) tmem_alloc(&tslot, 128);
   if (tid == 0) mbar_init(&mbar, 1);
   // the root table does not depend on earlier kernels: staged before the wait
   for (int i = tid; i < UW / 2; i += blockDim.x) cp_async<16>(roots + 2 * i, roots_g + 2 * i);
@@ -435,19 +437,21 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   tc_fence_after_sync();
   const uint32_t tm = tslot;
   // E_c entry (v, k) = root[(v_s a_k) mod UW], a_k = U s_x + k - K/2; this
-  // thread's operand rows: fine-grid point kq = tid / 8, columns 4 (tid % 8) + 0..3
-  const int kq = tid >> 3, vq = 4 * (tid & 7);
+  // thread's operand rows: fine-grid point kq, columns vq .. vq + 3 (a warp
+  // covers 8 consecutive kq and 4 column groups: conflict-free 16-byte stores)
+  const int kq = 8 * (warp & 3) + (tid & 7), vq = 4 * (4 * (warp >> 2) + ((tid & 31) >> 3));
   const int a_k = modp32(U * sx + kq - half, UW);
-  const uint32_t idesc = tc_idesc_tf32(kTcRows, 2 * kTcN, false);
-  uint64_t da[4][kTcKc / 8], db[4][kTcKc / 8];  // descriptors: plane x K step
+  const uint32_t id128 = tc_idesc_tf32(kTcRows, 4 * kTcN, false);
+  const uint32_t id64 = tc_idesc_tf32(kTcRows, 2 * kTcN, false);
+  uint64_t da[4][kTcKc / 8], db[2][kTcKc / 8];  // descriptors: plane x K step
   if (tid == 0) {
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int s = 0; s < kTcKc / 8; ++s) {
 #pragma unroll
-      for (int s = 0; s < kTcKc / 8; ++s) {
-        da[p][s] = tc_smem_desc(Ap + p * kTcAPlane + s * 256, 128, kTcSBO);
-        db[p][s] = tc_smem_desc(Bp + p * kTcBPlane + s * 256, 128, kTcSBO);
-      }
+      for (int p = 0; p < 4; ++p) da[p][s] = tc_smem_desc(Ap + p * kTcAPlane + s * 256, 128, kTcSBO);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) db[p][s] = tc_smem_desc(Bp + p * kTcBPlane + s * 256, 128, kTcSBO);
+    }
   }
   unsigned phase = 0;
   for (int c = 0; c < nch; ++c) {
@@ -466,7 +470,7 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
       cp_async_wait<0>();
       tc_fence_before_sync();
       __syncthreads();
-      if (warp == 0) tmem_dealloc(tm, 64);
+      if (warp == 0) tmem_dealloc(tm, 128);
       return;
     }
     {  // X split: thread -> row m, core-matrix columns q = 4 (tid / 128) + 0..3
@@ -488,7 +492,8 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
         *reinterpret_cast<float4*>(Ap + 3 * kTcAPlane + off) = il;
       }
     }
-    {  // E_c split: B1 = [Ecr | Eci], B2 = [-Eci | Ecr] (rows k and 32 + k)
+    {  // E_c split: B1 = [Ecr | Eci], B2 = [-Eci | Ecr] (rows k and 32 + k;
+       // their lo parts 64 rows further down)
       float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f}, nci[4];
       if (kq < K) {
         const int v0 = c * kTcKc + vq;  // 4 | W / 2: the four columns share a sign
@@ -509,14 +514,17 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
       split4(ci, ih, il);
       split4(nci, nh, nl);
       const int o1 = tc_off(kq, vq), o2 = tc_off(kTcN + kq, vq);
-      *reinterpret_cast<float4*>(Bp + o1) = rh;
-      *reinterpret_cast<float4*>(Bp + kTcBPlane + o1) = rl;
-      *reinterpret_cast<float4*>(Bp + o2) = ih;
-      *reinterpret_cast<float4*>(Bp + kTcBPlane + o2) = il;
-      *reinterpret_cast<float4*>(Bp + 2 * kTcBPlane + o1) = nh;
-      *reinterpret_cast<float4*>(Bp + 3 * kTcBPlane + o1) = nl;
-      *reinterpret_cast<float4*>(Bp + 2 * kTcBPlane + o2) = rh;
-      *reinterpret_cast<float4*>(Bp + 3 * kTcBPlane + o2) = rl;
+      const int l1 = tc_off(2 * kTcN + kq, vq), l2 = tc_off(3 * kTcN + kq, vq);
+      char* B1 = Bp;
+      char* B2 = Bp + kTcBPlane;
+      *reinterpret_cast<float4*>(B1 + o1) = rh;
+      *reinterpret_cast<float4*>(B1 + o2) = ih;
+      *reinterpret_cast<float4*>(B1 + l1) = rl;
+      *reinterpret_cast<float4*>(B1 + l2) = il;
+      *reinterpret_cast<float4*>(B2 + o1) = nh;
+      *reinterpret_cast<float4*>(B2 + o2) = rh;
+      *reinterpret_cast<float4*>(B2 + l1) = nl;
+      *reinterpret_cast<float4*>(B2 + l2) = rl;
     }
     fence_proxy_async();  // the planes, written through the generic proxy, go to the MMA
     __syncthreads();
@@ -525,12 +533,10 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
 #pragma unroll
       for (int s = 0; s < kTcKc / 8; ++s) {
         const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-        tc_mma_tf32(tm, da[0][s], db[0][s], idesc, acc);  // Xr hi B1 hi
-        tc_mma_tf32(tm, da[0][s], db[1][s], idesc, 1u);   // Xr hi B1 lo
-        tc_mma_tf32(tm, da[1][s], db[0][s], idesc, 1u);   // Xr lo B1 hi
-        tc_mma_tf32(tm, da[2][s], db[2][s], idesc, 1u);   // Xi hi B2 hi
-        tc_mma_tf32(tm, da[2][s], db[3][s], idesc, 1u);   // Xi hi B2 lo
-        tc_mma_tf32(tm, da[3][s], db[2][s], idesc, 1u);   // Xi lo B2 hi
+        tc_mma_tf32(tm, da[0][s], db[0][s], id128, acc);  // Xr hi [B1 hi | B1 lo]
+        tc_mma_tf32(tm, da[1][s], db[0][s], id64, 1u);    // Xr lo B1 hi
+        tc_mma_tf32(tm, da[2][s], db[1][s], id128, 1u);   // Xi hi [B2 hi | B2 lo]
+        tc_mma_tf32(tm, da[3][s], db[1][s], id64, 1u);    // Xi lo B2 hi
       }
       tc_commit(&mbar);
     }
@@ -541,17 +547,20 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
     if (!ok) mbar_wait_bounded(&mbar, phase, kLimit);
     tc_fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tm, 64);
+    if (warp == 0) tmem_dealloc(tm, 128);
     return;
   }
   tc_fence_after_sync();
-  {  // T -> shared memory: warps 0-3 Re T, 4-7 Im T of row 32 (warp % 4) + lane
-    float v[kTcN];
-    tmem_ld32(tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kTcN), v);
+  {  // T -> shared memory: warps 0-3 Re T, 4-7 Im T of row 32 (warp % 4) + lane,
+     // each the sum of the hi-hi + lo-hi and the hi-lo accumulator halves
+    float v[kTcN], w[kTcN];
+    const uint32_t ta = tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * kTcN);
+    tmem_ld32(ta, v);
+    tmem_ld32(ta + 2 * kTcN, w);
     const int m = 32 * (warp & 3) + (tid & 31);
     float* Tf = reinterpret_cast<float*>(T) + 2 * m * kTcTPitch + (warp >> 2);
 #pragma unroll
-    for (int k = 0; k < kTcN; ++k) Tf[2 * k] = v[k];
+    for (int k = 0; k < kTcN; ++k) Tf[2 * k] = v[k] + w[k];
   }
   // this block's E_r columns: Er[k1][r] = root[(u_s (U s_y + k1 - K/2)) mod UW]
   for (int t = tid; t < K * kTcRows; t += blockDim.x) {
@@ -563,7 +572,7 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   __syncthreads();
   if (warp == 0) {
     tc_fence_after_sync();
-    tmem_dealloc(tm, 64);
+    tmem_dealloc(tm, 128);
   }
   // share of this row block: sum_r E_r[k1][u0 + r] T[r][k2], 2 x 2 outputs per thread
   float2* dst = part + ((size_t)lp * gridDim.x + blockIdx.x) * K * K;

@@ -95,13 +95,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x = hi + lo with hi = x rounded to TF32 (nearest, ties away) and lo the
-// exact remainder, itself taken as TF32 by the MMA: the three products
-// hi hi + hi lo + lo hi carry about 21 bits of each operand.
+// x = hi + lo with hi = x cut to a TF32 value (its low 13 mantissa bits
+// cleared) and lo = x - hi, exact in FP32 and itself taken as TF32 by the
+// MMA: the three products hi hi + hi lo + lo hi carry about 21 bits of each
+// operand.
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  hi = __uint_as_float(h);
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
   lo = x - hi;
 }
 
