@@ -65,7 +65,7 @@ def per_pass_flops(W, M):
 # `bench.py --workload spiral_256_n2000` (256^2 x 5 modes; launches 31-60 of
 # the three passes, groups 10-19, 133 patches).  Valid for the pass kernels as
 # profiled; a launch's traffic is this times its patches.
-DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.200e6, "cols": 0.357e6, "rows_inv": 0.099e6}}
+DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.226e6, "cols": 0.378e6, "rows_inv": 0.096e6}}
 
 
 def fp32_peak_tflops():
