@@ -165,6 +165,27 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def batch_shard(costs, rank, world):
+    """Problems of the batched workload that `rank` runs: longest processing
+    time first onto the least-loaded rank (ties to the lower rank), so every
+    rank gets a near-equal share of the work and each problem runs on exactly
+    one rank.  `costs` is any per-problem work estimate."""
+    load = [0.0] * world
+    mine = []
+    for p in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += costs[p]
+        if r == rank:
+            mine.append(p)
+    return sorted(mine)
+
+
+def problem_cost(wl):
+    """Work of one M-rPIE iteration of a problem, in flops (2M 2-D DFTs per patch)."""
+    import math
+    return wl.N * wl.M * wl.W * wl.W * math.log2(wl.W * wl.W)
+
+
 def replica_rate(units_per_rank, seconds_per_rank, world):
     """Whole-job throughput of `world` independent replicas: all units over
     the slowest rank's time (weak scaling)."""
@@ -423,7 +444,7 @@ def run_ours(args, wl, rank, world, local):
         prob.orthogonalize_probe()
     ortho_ms = (time.perf_counter() - t0) / 5 * 1e3
 
-    batch = run_batch_measure(args, dev) if not args.no_batch else None
+    batch = run_batch_measure(args, dev, rank, world) if not args.no_batch else None
     # measured FP32 FMA throughput, beside the nominal peak (after the timed work)
     ffma = pty.measure_fp32_peak()
 
@@ -464,36 +485,50 @@ def run_ours(args, wl, rank, world, local):
     return out
 
 
-def run_batch_measure(args, dev, n_iter=5):
-    """The 64-problem uneven batch (W in {64,96,128,192}, N 50..900, M 1..3)
-    in one persistent graph-captured launch: aggregate pattern-updates/s."""
+def run_batch_measure(args, dev, rank=0, world=1, n_iter=50):
+    """The 64-problem uneven batch (W in {64,96,128,192}, N 50..900, M 1..3),
+    50 M-rPIE iterations each, in one persistent graph-captured launch per
+    rank: aggregate pattern-updates/s.  With several ranks the problems are
+    split between them (batch_shard; independent problems: no data-path
+    collective, the timing takes the slowest rank), so the total work is
+    fixed as ranks are added.  The task granularity and the position-group
+    schedule (a cap on the group size) come from the autotuner's table."""
     import torch
-    from paper_2205_04295_b300 import pty, synth
-    wls = [synth.batch_problem(p) for p in range(64)]
+    from paper_2205_04295_b300 import autotune, pty, synth
+    all_wls = [synth.batch_problem(p) for p in range(64)]
+    mine = batch_shard([problem_cost(w) for w in all_wls], rank, world)
+    wls = [all_wls[p] for p in mine]
+    tuned = autotune.batch_schedule()
     b = pty.Batch([(w.W, w.M, w.N, w.Hy, w.Hx) for w in wls])
+    if tuned:
+        b.schedule(**tuned["schedule"])
     for w, p in zip(wls, b.problems):
         d = synth.build(w, device=dev)
         p.set_data(synth.counts_u16(d["I"]), torch.from_numpy(d["pos"]).to(dev),
                    torch.from_numpy(d["O0"]).to(dev), torch.from_numpy(d["P0"]).to(dev))
-    prm = pty.rpie_params()
+    prm = pty.rpie_params(max_group=tuned["max_group"] if tuned else 0)
     b.run(1, prm)
     torch.cuda.synchronize()
+    barrier(world)
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     b.run(n_iter, prm)
     e.record()
     torch.cuda.synchronize()
-    ms = a.elapsed_time(e)
-    n = sum(w.N for w in wls) * n_iter
+    ms = max_over_ranks(a.elapsed_time(e), world)
+    n = sum(w.N for w in all_wls) * n_iter
     b.close()
     # the same problems one after another, each through pty_run_iterations
     # with its own tuned per-pass launches
-    seq_ms = run_sequential(wls, dev, n_iter, prm)
+    seq_ms = max_over_ranks(run_sequential(wls, dev, n_iter, prm), world)
     return {"problems": 64, "iterations": n_iter, "pattern_updates": n, "ms": ms,
-            "value": n / (ms / 1e3), "unit": UNIT, "launches": 1,
+            "value": n / (ms / 1e3), "unit": UNIT, "launches": 1, "ranks": world,
+            "scaling": "strong" if world > 1 else None,
+            "schedule": tuned,
             "sequential": {"ms": seq_ms, "value": n / (seq_ms / 1e3), "unit": UNIT,
-                           "what": "the 64 problems one after another, pty_run_iterations each"},
-            "what": "one persistent cooperative launch (a CUDA graph) for all problems and iterations"}
+                           "what": "the same problems one after another, pty_run_iterations each"},
+            "what": "one persistent cooperative launch (a CUDA graph) per rank for all its "
+                    "problems and iterations"}
 
 
 def run_sequential(wls, dev, n_iter, prm):

@@ -83,24 +83,55 @@ def tune_problem(prob, params=None, reps=2):
     return {"tiling": best, "ms": best_ms, "trials": trials}
 
 
-def tune_batch(batch, n_iter=1, params=None):
-    """Task granularity of the batched form: returns the best schedule."""
+def tune_batch(batch, n_iter=1, params=None, caps=(0, 32, 16, 8)):
+    """Task granularity and position-group schedule of the batched form.
+
+    Stage 1 times the task splits with unlimited groups; stage 2 times caps
+    on the number of positions per disjoint group (0 = the greedy groups as
+    they come; a cap makes more, smaller groups: more dependency steps, but
+    finer tasks for the persistent kernel to balance).  A different cap is a
+    different schedule of the same method (the oracle takes the same
+    ``max_group``), so parity tests run with the chosen cap on both sides.
+    The problems' state advances with every trial; only times are compared.
+    Returns {"schedule": splits, "max_group": cap, "s": seconds, "trials": [...]}."""
     import time
     import torch
     params = params or pty.rpie_params()
-    best = None
-    for sr, sc, sp in ((1, 1, 1), (2, 1, 2), (4, 2, 4), (8, 2, 4), (8, 4, 8), (16, 8, 8)):
-        batch.schedule(split_rows=sr, split_cols=sc, split_probe=sp)
-        batch.run(n_iter, params)
+    trials = []
+
+    def timed(cap):
+        p = pty.rpie_params(params.alpha_O, params.alpha_P, params.beta, params.gamma,
+                            params.eps, params.reg_eps, cap, bool(params.update_probe))
+        batch.run(n_iter, p)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        batch.run(n_iter, params)
+        batch.run(n_iter, p)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        return time.perf_counter() - t0
+
+    best = None
+    for sr, sc, sp in ((1, 1, 1), (2, 1, 2), (4, 2, 4), (8, 2, 4), (8, 4, 8), (16, 8, 8)):
+        sched = dict(split_rows=sr, split_cols=sc, split_probe=sp)
+        batch.schedule(**sched)
+        dt = timed(0)
+        trials.append(dict(sched, max_group=0, s=dt))
         if best is None or dt < best[0]:
-            best = (dt, dict(split_rows=sr, split_cols=sc, split_probe=sp))
+            best = (dt, sched, 0)
     batch.schedule(**best[1])
-    return {"schedule": best[1], "s": best[0]}
+    for cap in caps:
+        if cap == 0:
+            continue
+        dt = timed(cap)
+        trials.append(dict(best[1], max_group=cap, s=dt))
+        if dt < best[0]:
+            best = (dt, best[1], cap)
+    return {"schedule": best[1], "max_group": best[2], "s": best[0], "trials": trials}
+
+
+def batch_schedule(table=None):
+    """The cached batched-form choice ({"schedule": ..., "max_group": ...}), or None."""
+    table = load() if table is None else table
+    return table.get("batch")
 
 
 def load(path=CACHE):
@@ -145,9 +176,11 @@ def main():
     ap.add_argument("--classes", default="256x5,256x4,64x1,64x2,64x3,96x1,96x2,96x3,128x1,"
                                         "128x2,128x3,192x1,192x2,192x3")
     ap.add_argument("--out", default=CACHE)
+    ap.add_argument("--batch", action="store_true",
+                    help="also tune the 64-problem batched workload (task splits, group cap)")
     args = ap.parse_args()
     table = load(args.out)
-    for cls in args.classes.split(","):
+    for cls in filter(None, args.classes.split(",")):
         W, M = (int(v) for v in cls.split("x"))
         wl = _workload(W, M)
         d = synth.build(wl, device="cuda")
@@ -159,6 +192,18 @@ def main():
         table[cls] = res
         print(cls, res["tiling"], "%.3f ms" % res["ms"], flush=True)
         prob.close()
+    if args.batch:
+        wls = [synth.batch_problem(p) for p in range(64)]
+        b = pty.Batch([(w.W, w.M, w.N, w.Hy, w.Hx) for w in wls])
+        for w, p in zip(wls, b.problems):
+            d = synth.build(w, device="cuda")
+            p.set_data(synth.counts_u16(d["I"]), torch.from_numpy(d["pos"]).cuda(),
+                       torch.from_numpy(d["O0"]).cuda(), torch.from_numpy(d["P0"]).cuda())
+        res = tune_batch(b, n_iter=2)
+        res["workload"] = "64-problem uneven batch"
+        table["batch"] = res
+        print("batch", res["schedule"], "max_group", res["max_group"], "%.3f s" % res["s"], flush=True)
+        b.close()
     save(table, args.out)
 
 

@@ -11,3 +11,17 @@ def test_oracle_sample_and_all_core_figure():
     assert rate > 0 and done > 0 and ng >= 1
     r = bench.oracle_all_cores(wl, 2, 0.5)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
+
+
+def test_batch_shard_partitions_and_balances():
+    """Every problem of the batched workload runs on exactly one rank, and the
+    ranks' shares of the work are near-equal (longest first, least loaded)."""
+    import bench
+    wls = [synth.batch_problem(p) for p in range(64)]
+    costs = [bench.problem_cost(w) for w in wls]
+    for world in (1, 2, 4, 8):
+        shards = [bench.batch_shard(costs, r, world) for r in range(world)]
+        flat = sorted(p for s in shards for p in s)
+        assert flat == list(range(64))
+        loads = [sum(costs[p] for p in s) for s in shards]
+        assert max(loads) <= 1.1 * sum(costs) / world + max(costs)

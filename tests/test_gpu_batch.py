@@ -71,6 +71,28 @@ def test_batch_50_iterations_against_the_oracle():
     b.close()
 
 
+def test_group_cap_schedule_matches_standalone_and_oracle():
+    """The autotuner may cap the positions per disjoint group (a different,
+    equally valid schedule): with the same cap the batched form equals the
+    standalone runs bitwise and the oracle (max_group on its side too)."""
+    from paper_2205_04295_b300 import pty
+    wls = small_mix()[:3]
+    ds = [build(w) for w in wls]
+    b = run_batch(wls, ds, 3)
+    b.run(3, pty.rpie_params(max_group=4))
+    assert list(b.status()) == [0] * len(wls)
+    for k, (w, d) in enumerate(zip(wls, ds)):
+        solo = pty.Problem(w.W, w.M, w.N, w.Hy, w.Hx)
+        solo.set_data(d["I"], d["pos"], d["O0"], d["P0"])
+        solo.run(3, pty.rpie_params(max_group=4))
+        np.testing.assert_array_equal(b.problems[k].object(False), solo.object(False))
+        st = rpie.State.create(d["O0"], d["P0"], d["pos"])
+        rpie.run(st, d["I"], rpie.RPIEParams(max_group=4), 3)
+        assert rel_l2(b.problems[k].object(False), st.O) <= 1e-4
+        assert rel_l2(b.problems[k].probe(False), st.P) <= 1e-4
+    b.close()
+
+
 def test_schedule_variants_give_identical_results():
     wls = small_mix()[:4]
     ds = [build(w) for w in wls]
