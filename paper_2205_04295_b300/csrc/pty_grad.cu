@@ -30,25 +30,6 @@ PTY_D float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-// Block-wide sums of two values at once; every thread gets them.  Contains barriers.
-PTY_D float2 block_sum2(float2 v, float* red) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  v.x = warp_sum(v.x);
-  v.y = warp_sum(v.y);
-  __syncthreads();
-  if (l == 0) {
-    red[2 * w] = v.x;
-    red[2 * w + 1] = v.y;
-  }
-  __syncthreads();
-  float2 t = make_float2(0.f, 0.f);
-  for (int i = 0; i < nw; ++i) {  // fixed order
-    t.x += red[2 * i];
-    t.y += red[2 * i + 1];
-  }
-  return t;
-}
-
 struct Bil {
   int iy, ix;
   float fy, fx;
@@ -188,7 +169,10 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
   float2* st = obuf + R * W;        // 2 x (R + 1) x (W + 1) object rows
   Bil* sb = reinterpret_cast<Bil*>(st + 2 * (R + 1) * SP);  // ppc crop geometries
   int* sj = reinterpret_cast<int*>(sb + ppc);                // ppc pattern ids
-  __shared__ float red2[64];
+  // per patch and warp, the warp's (dL/dy, dL/dx) share: summed over the
+  // warps in a fixed order once after the patch loop, so the patches need no
+  // block reduction of their own
+  float* gw = reinterpret_cast<float*>(sj + ppc);            // ppc x 8 x 2
   const int r0 = blockIdx.x * R, nrb = W / R;
   const int p0 = blockIdx.y * ppc, p1 = min(npatch, p0 + ppc);
   pdl_trigger();
@@ -218,7 +202,6 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
   const int k = act ? line / R : 0, r = act ? line - k * R : 0;
   float2* lbuf = tbuf + line * G::LP;
   for (int lp = p0; lp < p1; ++lp) {
-    const int j = sj[lp - p0];
     const Bil b = sb[lp - p0];
     const float2* sc = st + ((lp - p0) & 1) * (R + 1) * SP;
     cp_async_wait<0>();
@@ -263,14 +246,27 @@ k_grad_rows_inv(const float2* __restrict__ O, int Hx, const float2* __restrict__
       gx += g.x * dx.x + g.y * dx.y;
       gout[(size_t)rr * W + c] = g;
     }
-    const float2 gs = block_sum2(make_float2(gy, gx), red2);
-    if (threadIdx.x == 0) {
-      gpos_part[((size_t)j * nrb + blockIdx.x) * 2] = gs.x;
-      gpos_part[((size_t)j * nrb + blockIdx.x) * 2 + 1] = gs.y;
+    gy = warp_sum(gy);
+    gx = warp_sum(gx);
+    if ((threadIdx.x & 31) == 0) {
+      gw[((lp - p0) * 8 + (threadIdx.x >> 5)) * 2] = gy;
+      gw[((lp - p0) * 8 + (threadIdx.x >> 5)) * 2 + 1] = gx;
     }
   }
   cp_async_wait<0>();
   __syncthreads();
+  {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int t = threadIdx.x; t < p1 - p0; t += blockDim.x) {
+      float sy = 0.f, sx = 0.f;
+      for (int w = 0; w < nw; ++w) {  // fixed order
+        sy += gw[(t * 8 + w) * 2];
+        sx += gw[(t * 8 + w) * 2 + 1];
+      }
+      gpos_part[((size_t)sj[t] * nrb + blockIdx.x) * 2] = sy;
+      gpos_part[((size_t)sj[t] * nrb + blockIdx.x) * 2 + 1] = sx;
+    }
+  }
   const int slot = blockIdx.y;
   for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
     const int kk = e / (R * W), rem = e - kk * R * W, rr = rem / W, c = rem - rr * W;
@@ -373,7 +369,7 @@ static size_t grad_inv_smem(const Tiling& t) {
   const int TB = std::max(t.M * t.R * LP, t.M * t.R * t.W);
   return (size_t)(t.W + t.M * t.R * t.W + TB + t.M * t.R * t.W + t.R * t.W +
                   2 * (t.R + 1) * (t.W + 1)) * sizeof(float2) +
-         (size_t)t.ppc * (sizeof(Bil) + sizeof(int));
+         (size_t)t.ppc * (sizeof(Bil) + sizeof(int) + 8 * 2 * sizeof(float));
 }
 
 static size_t grad_fwd_smem(const Tiling& t) {
