@@ -241,6 +241,7 @@ struct pty_handle {
   pty::RefGeo rg{};
   float2* roots = nullptr;
   float2* upart = nullptr;  // fine-grid partial sums of the registration
+  int* updone = nullptr;     // N counters of finished CTAs per patch (tensor-core form)
   int roots_U = 0;
   float *cval = nullptr, *gap = nullptr;
   int* cidx = nullptr;
@@ -504,7 +505,8 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0) {
       CU(pty::launch_xcorr_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->cval, h->cidx,
                                 h->stream));
       CU(pty::launch_updft(h->rg, h->scratch, tl.npl, h->M, idc, nc, h->cval, h->cidx,
-                           h->roots, h->upart, h->shift, h->gap, h->tma_err, h->stream));
+                           h->roots, h->upart, h->shift, h->gap, h->updone, h->tma_err,
+                           h->stream));
       h->n_launch[PTY_K_REFINE] += 2;
     }
   }
@@ -775,6 +777,7 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
       (rc = alloc_into(h, h->cval, nparts)) ||
       (rc = alloc_into(h, h->cidx, nparts)) ||
       (rc = alloc_into(h, h->gap, (size_t)h->N)) ||
+      (rc = alloc_into(h, h->updone, (size_t)h->N)) ||
       (rc = alloc_into(h, h->pnum, (size_t)h->nslots * h->M * W2)) ||
       (rc = alloc_into(h, h->pden, (size_t)h->nslots * W2)) ||
       (rc = alloc_into(h, h->osum, (size_t)h->nslots)) ||
@@ -992,6 +995,9 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
     h->roots_U = r->upsample;
   }
   if (n_iter == 0) return PTY_OK;
+  // the fine-grid kernels' per-patch counters start at zero (each launch
+  // leaves them there; this also clears them after a launch that gave up)
+  CU(cudaMemsetAsync(h->updone, 0, sizeof(int) * h->N, h->stream));
   TRY(ensure_err_cap(h, n_iter));
   for (int it = 0; it < n_iter; ++it) {
     TRY(regroup(h, p->max_group));

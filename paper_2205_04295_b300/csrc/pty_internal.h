@@ -154,10 +154,12 @@ cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, i
                               int npatch, const float2* tw, float* cval, int* cidx,
                               cudaStream_t s);
 // part: npatch * (W / 16) * K * K complex partial sums of the fine grid;
-// err: status word set by a tensor-core wait that gave up
+// done: npatch zeroed counters (the tensor-core form's last-CTA detection,
+// left at zero); err: status word set by a tensor-core wait that gave up
 cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
                          int npatch, const float* cval, const int* cidx, const float2* roots,
-                         float2* part, float* shift, float* gap, int* err, cudaStream_t s);
+                         float2* part, float* shift, float* gap, int* done, int* err,
+                         cudaStream_t s);
 cudaError_t launch_adam(float* pos, float* m, float* v, const float* g, int N, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, float max_step,
                         float ymax, float xmax, cudaStream_t s);

@@ -94,24 +94,26 @@ k_xcorr_cols(float2* __restrict__ scratch, int npl, int M, int CB,
   float2* colA = scratch + ((size_t)lp * npl + M) * W * W + c0 + c;
   float2* colB = colA + (size_t)W * W;
   float2* lbuf = tbuf + c * G::LP;
-  // both columns are requested together
-  float2 v[G::N1], vb[G::N1];
+  // the first crop's column; the second one is loaded once the first is
+  // transformed, so that only one column is held in registers at a time
+  float2 v[G::N1];
   if (act && lane < G::N2) {
 #pragma unroll
-    for (int n1 = 0; n1 < G::N1; ++n1) {
-      v[n1] = colA[(size_t)(G::N2 * n1 + lane) * W];
-      vb[n1] = colB[(size_t)(G::N2 * n1 + lane) * W];
-    }
+    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = colA[(size_t)(G::N2 * n1 + lane) * W];
   }
   __syncthreads();
   // A = F(o_j): the column DFTs of plane M (its row DFTs come from pass A)
   if (act && lane < G::N2) fwd_step1<W>(v, lane, tw, lbuf);
+  if (act && lane < G::N2) {
+#pragma unroll
+    for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = colB[(size_t)(G::N2 * n1 + lane) * W];
+  }
   __syncthreads();
   float2 za[G::N2];
   if (act && lane < G::N1) fwd_step3<W>(za, lane, lbuf);
   __syncthreads();
   // B = F(o'_j)
-  if (act && lane < G::N2) fwd_step1<W>(vb, lane, tw, lbuf);
+  if (act && lane < G::N2) fwd_step1<W>(v, lane, tw, lbuf);
   __syncthreads();
   float2 z[G::N2];
   if (act && lane < G::N1) {
@@ -333,6 +335,46 @@ k_updft_part(const float2* __restrict__ scratch, int npl, int M, int nparts,
   }
 }
 
+// Sum of a patch's fine-grid shares in block order, |c_up|^2, its first
+// maximum in row-major order and the gap to the second best; writes the
+// measurement g_j = -shift of pattern j.  Contains barriers.
+PTY_D void updft_finish(int lp, int j, int sy, int sx, int nblocks, int U, int K,
+                        const float2* part, float* shift, float* gap, float* rv, int* ri) {
+  const int half = K / 2;
+  float best = -1.f, second = -1.f;
+  int bi = 0x7fffffff;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = 0; b < nblocks; ++b)  // fixed order
+      acc = cadd(acc, __ldcg(part + ((size_t)lp * nblocks + b) * K * K + e));
+    const float m = cabs2(acc);
+    if (m > best) {
+      second = fmaxf(second, best);
+      best = m;
+      bi = e;
+    } else {
+      second = fmaxf(second, m);
+    }
+  }
+  float gb = best;
+  int gbi = bi;
+  block_best(gb, gbi, rv, ri);
+  float s2 = (bi == gbi) ? second : best;  // best of this thread that is not the winner
+  __syncthreads();
+  {
+    int dummy = 0;
+    block_best(s2, dummy, rv, ri);
+  }
+  if (threadIdx.x == 0) {
+    const int k1 = gbi / K, k2 = gbi % K;
+    const float y = (float)sy + (float)(k1 - half) / (float)U;
+    const float x = (float)sx + (float)(k2 - half) / (float)U;
+    shift[2 * j] = -y;
+    shift[2 * j + 1] = -x;
+    gap[j] = gb > 0.f ? (gb - fmaxf(s2, 0.f)) / gb : 0.f;
+  }
+}
+
 // ------------------------------------------------------------ updft_tc
 // Tensor-core form of updft_part (tcgen05, kind::tf32, 3xTF32 split): CTA
 // (tile of 128 rows of X, patch).  T = X_rows E_c is taken on the
@@ -344,28 +386,34 @@ k_updft_part(const float2* __restrict__ scratch, int npl, int M, int nparts,
 // along N (rows 0-63 hi, 64-127 lo), so per K step one N = 128 MMA takes
 // X_hi [B_hi | B_lo] and one N = 64 MMA adds X_lo B_hi into the first half:
 // the 128 x 128 FP32 accumulator in TMEM holds [hi-hi + lo-hi | hi-lo]
-// products, added at read-out.  X is staged by cp.async one chunk of 32
-// columns ahead and split into four K-major planes (Xr hi, Xr lo, Xi hi,
-// Xi lo), the matching chunk of the two stacked E_c operands into two more;
-// one thread issues the chunk's 16 MMAs and commits them to an mbarrier
-// (bounded wait).  The phases exp(2 pi i n / (U W)) come from the root
+// products, added at read-out.
+//
+// Pipeline over chunks of 16 columns of X: X is staged by cp.async two
+// chunks ahead; a chunk is split into four K-major planes (Xr hi, Xr lo,
+// Xi hi, Xi lo) and the matching chunk of the two stacked E_c operands into
+// two more, in one of two plane buffers; one thread issues the chunk's 8
+// MMAs and commits them to that buffer's mbarrier, and the CTA goes on to
+// split the next chunk into the other buffer while they run (a buffer is
+// refilled once its mbarrier says the MMAs that read it are done; every
+// wait is bounded).  The phases exp(2 pi i n / (U W)) come from the root
 // table, staged into shared memory before the dependency wait; their indices
 // are stepped in 32-bit integers.  The block's share E_r[:, rows] T (K x K)
 // is then taken on the FP32 cores (2 x 2 outputs per thread) from T copied
 // to shared memory, and updft_final adds the shares.  Rows past W (W < 128,
 // or the second tile at W = 192) are zero.
 constexpr int kTcRows = 128;                  // M of the MMA: rows of X per CTA
-constexpr int kTcKc = 32;                     // columns of X (index v) per chunk
+constexpr int kTcKc = 16;                     // columns of X (index v) per chunk
 constexpr int kTcN = 32;                      // fine-grid points held (K <= 32)
-constexpr int kTcRawPitch = kTcKc + 2;        // complex per staged row (272 B)
+constexpr int kTcRawPitch = kTcKc + 2;        // complex per staged row (144 B)
 constexpr int kTcTPitch = kTcN + 1;           // complex per row of T in shared memory
-constexpr int kTcAPlane = kTcRows * kTcKc * 4;    // bytes of one A plane (128 x 32)
-constexpr int kTcBPlane = 4 * kTcN * kTcKc * 4;   // bytes of one stacked B plane (128 x 32)
+constexpr int kTcAPlane = kTcRows * kTcKc * 4;    // bytes of one A plane (128 x 16)
+constexpr int kTcBPlane = 4 * kTcN * kTcKc * 4;   // bytes of one stacked B plane (128 x 16)
+constexpr int kTcBuf = 4 * kTcAPlane + 2 * kTcBPlane;  // one set of operand planes
 constexpr int kTcSBO = (kTcKc / 4) * 128;         // bytes between 8-row groups
 constexpr int kTcRaw = 2 * kTcRows * kTcRawPitch * 8;
-constexpr int kTcFixed = kTcRaw + 4 * kTcAPlane + 2 * kTcBPlane + 128;  // + the root table
+constexpr int kTcFixed = kTcRaw + 2 * kTcBuf + 128;  // + the root table
 static_assert(kTcRows * kTcTPitch * 8 <= kTcRaw, "T reuses the staging buffers");
-static_assert(kTcN * kTcRows * 8 <= 4 * kTcAPlane, "E_r reuses the A planes");
+static_assert(kTcN * kTcRows * 8 <= 2 * kTcBuf, "E_r reuses the operand planes");
 
 // Byte offset of element (row, k) in a K-major, no-swizzle plane of kTcKc
 // columns: core matrices (8 rows x 4 values, 128 bytes) with the K-adjacent
@@ -390,20 +438,20 @@ __global__ void __launch_bounds__(256, 1)
 k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
            const float* __restrict__ cval, const int* __restrict__ cidx,
            const float2* __restrict__ roots_g, int U, int K, float2* __restrict__ part,
-           int* __restrict__ err) {
+           const int* __restrict__ ids, int* __restrict__ done, float* __restrict__ shift,
+           float* __restrict__ gap, int* __restrict__ err) {
   extern __shared__ float4 smem4[];
-  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ uint32_t tslot;
   __shared__ float rv[32];
   __shared__ int ri[32];
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem4) + 127) &
                                        ~static_cast<uintptr_t>(127));
   float2* raw = reinterpret_cast<float2*>(base);   // 2 x [128][kTcRawPitch]
-  char* Ap = base + kTcRaw;                         // Xr hi, Xr lo, Xi hi, Xi lo
-  char* Bp = Ap + 4 * kTcAPlane;                    // [B1 hi; B1 lo], [B2 hi; B2 lo]
-  float2* roots = reinterpret_cast<float2*>(Bp + 2 * kTcBPlane);  // U W roots
+  char* pl = base + kTcRaw;                         // 2 x (Xr hi, Xr lo, Xi hi, Xi lo, B1, B2)
+  float2* roots = reinterpret_cast<float2*>(pl + 2 * kTcBuf);  // U W roots
   float2* T = raw;                                  // [128][kTcTPitch] after the MMAs
-  float2* Er = reinterpret_cast<float2*>(Ap);       // [K][128] after the MMAs
+  float2* Er = reinterpret_cast<float2*>(pl);       // [K][128] after the MMAs
 
   const int lp = blockIdx.y, u0 = blockIdx.x * kTcRows;
   const int nrows = min(kTcRows, W - u0);
@@ -414,7 +462,10 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   constexpr unsigned long long kLimit = 200000000ull;  // 0.2 s of the global timer
   pdl_trigger();
   if (warp == 0) tmem_alloc(&tslot, 128);
-  if (tid == 0) mbar_init(&mbar, 1);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
   // the root table does not depend on earlier kernels: staged before the wait
   for (int i = tid; i < UW / 2; i += blockDim.x) cp_async<16>(roots + 2 * i, roots_g + 2 * i);
   cp_async_commit();
@@ -423,65 +474,65 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   for (int i = tid; i < 2 * zr; i += blockDim.x)
     raw[(i / zr) * kTcRows * kTcRawPitch + nrows * kTcRawPitch + i % zr] = make_float2(0.f, 0.f);
   pdl_wait();  // X and the coarse peaks come from the correlation passes
-  auto stage = [&](int c, int b) {
-    float2* dst = raw + b * kTcRows * kTcRawPitch;
-    for (int i = tid; i < nrows * (kTcKc / 2); i += blockDim.x) {
-      const int r = i / (kTcKc / 2), h = i - r * (kTcKc / 2);
-      cp_async<16>(dst + r * kTcRawPitch + 2 * h, X + (size_t)r * W + c * kTcKc + 2 * h);
+  auto stage = [&](int c) {
+    if (c < nch) {
+      float2* dst = raw + (c & 1) * kTcRows * kTcRawPitch;
+      for (int i = tid; i < nrows * (kTcKc / 2); i += blockDim.x) {
+        const int r = i / (kTcKc / 2), h = i - r * (kTcKc / 2);
+        cp_async<16>(dst + r * kTcRawPitch + 2 * h, X + (size_t)r * W + c * kTcKc + 2 * h);
+      }
     }
+    cp_async_commit();  // one group per chunk, empty past the last
   };
-  stage(0, 0);
-  cp_async_commit();
+  stage(0);
+  stage(1);
   int sy, sx;
   coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);  // contains barriers
   tc_fence_after_sync();
   const uint32_t tm = tslot;
-  // E_c entry (v, k) = root[(v_s a_k) mod UW], a_k = U s_x + k - K/2; this
-  // thread's operand rows: fine-grid point kq, columns vq .. vq + 3 (a warp
-  // covers 8 consecutive kq and 4 column groups: conflict-free 16-byte stores)
-  const int kq = 8 * (warp & 3) + (tid & 7), vq = 4 * (4 * (warp >> 2) + ((tid & 31) >> 3));
+  // E_c entry (v, k) = root[(v_s a_k) mod UW], a_k = U s_x + k - K/2; threads
+  // 0-127 write the operand rows of fine-grid point kq, columns vq .. vq + 3
+  // (a warp covers 8 consecutive kq and the 4 column groups: conflict-free)
+  const int kq = 8 * (warp & 3) + (tid & 7), vq = 4 * ((tid & 31) >> 3);
   const int a_k = modp32(U * sx + kq - half, UW);
   const uint32_t id128 = tc_idesc_tf32(kTcRows, 4 * kTcN, false);
   const uint32_t id64 = tc_idesc_tf32(kTcRows, 2 * kTcN, false);
-  uint64_t da[4][kTcKc / 8], db[2][kTcKc / 8];  // descriptors: plane x K step
-  if (tid == 0) {
-#pragma unroll
-    for (int s = 0; s < kTcKc / 8; ++s) {
-#pragma unroll
-      for (int p = 0; p < 4; ++p) da[p][s] = tc_smem_desc(Ap + p * kTcAPlane + s * 256, 128, kTcSBO);
-#pragma unroll
-      for (int p = 0; p < 2; ++p) db[p][s] = tc_smem_desc(Bp + p * kTcBPlane + s * 256, 128, kTcSBO);
-    }
-  }
-  unsigned phase = 0;
-  for (int c = 0; c < nch; ++c) {
+  // descriptors of buffer 0; the other planes differ only in the start field
+  // (address / 16, well inside its 14 bits)
+  const uint64_t d0 = tc_smem_desc(pl, 128, kTcSBO);
+  unsigned ph = 0u;  // bit b: parity of the next completion of mbar[b]
+  auto fail = [&](bool mine, int b) {
+    if (tid == 0) atomicExch(err, 1);
+    if (mine) mbar_wait_bounded(&mbar[b], ((ph >> b) & 1u) ^ 1u, kLimit);  // the MMAs in flight
     cp_async_wait<0>();
-    __syncthreads();  // chunk c (and the roots) have landed; the split of chunk c - 1 is done
-    if (c + 1 < nch) stage(c + 1, (c + 1) & 1);
-    cp_async_commit();
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tm, 128);
+  };
+  for (int c = 0; c < nch; ++c) {
+    const int b = c & 1;
+    cp_async_wait<1>();
+    __syncthreads();  // chunk c has landed
     bool ok = true;
-    if (c > 0) {  // the MMAs of chunk c - 1 still read the planes
-      ok = mbar_wait_bounded(&mbar, phase, kLimit);
-      phase ^= 1;
+    if (c >= 2) {  // the MMAs of chunk c - 2 still read plane buffer b
+      ok = mbar_wait_bounded(&mbar[b], (ph >> b) & 1u, kLimit);
+      ph ^= 1u << b;
     }
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicExch(err, 1);
-      if (!ok) mbar_wait_bounded(&mbar, phase ^ 1, kLimit);  // the MMAs in flight
-      cp_async_wait<0>();
-      tc_fence_before_sync();
-      __syncthreads();
-      if (warp == 0) tmem_dealloc(tm, 128);
+      fail(!ok, b);
       return;
     }
-    {  // X split: thread -> row m, core-matrix columns q = 4 (tid / 128) + 0..3
+    char* Ap = pl + b * kTcBuf;
+    char* Bp = Ap + 4 * kTcAPlane;
+    {  // X split: thread -> row m, core-matrix columns q = 2 (tid / 128) + 0..1
       const int m = tid & (kTcRows - 1);
-      const float2* src = raw + (c & 1) * kTcRows * kTcRawPitch + m * kTcRawPitch;
+      const float2* src = raw + b * kTcRows * kTcRawPitch + m * kTcRawPitch;
 #pragma unroll
-      for (int qq = 0; qq < kTcKc / 8; ++qq) {
-        const int q = (kTcKc / 8) * (tid >> 7) + qq;
-        const float4 a = *reinterpret_cast<const float4*>(src + 4 * q);
-        const float4 b = *reinterpret_cast<const float4*>(src + 4 * q + 2);
-        const float re[4] = {a.x, a.z, b.x, b.z}, im[4] = {a.y, a.w, b.y, b.w};
+      for (int qq = 0; qq < 2; ++qq) {
+        const int q = 2 * (tid >> 7) + qq;
+        const float4 x0 = *reinterpret_cast<const float4*>(src + 4 * q);
+        const float4 x1 = *reinterpret_cast<const float4*>(src + 4 * q + 2);
+        const float re[4] = {x0.x, x0.z, x1.x, x1.z}, im[4] = {x0.y, x0.w, x1.y, x1.w};
         float4 rh, rl, ih, il;
         split4(re, rh, rl);
         split4(im, ih, il);
@@ -492,8 +543,7 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
         *reinterpret_cast<float4*>(Ap + 3 * kTcAPlane + off) = il;
       }
     }
-    {  // E_c split: B1 = [Ecr | Eci], B2 = [-Eci | Ecr] (rows k and 32 + k;
-       // their lo parts 64 rows further down)
+    if (tid < 4 * kTcN) {  // E_c split: B1 = [Ecr | Eci], B2 = [-Eci | Ecr], lo parts 64 rows down
       float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f}, nci[4];
       if (kq < K) {
         const int v0 = c * kTcKc + vq;  // 4 | W / 2: the four columns share a sign
@@ -530,26 +580,34 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
     __syncthreads();
     if (tid == 0) {
       tc_fence_after_sync();
+      const uint64_t db = d0 + (uint64_t)((b * kTcBuf) >> 4);
 #pragma unroll
       for (int s = 0; s < kTcKc / 8; ++s) {
+        const uint64_t ds = db + (uint64_t)((s * 256) >> 4);
+        const uint64_t xrh = ds, xrl = ds + (kTcAPlane >> 4);
+        const uint64_t xih = ds + ((2 * kTcAPlane) >> 4), xil = ds + ((3 * kTcAPlane) >> 4);
+        const uint64_t b1 = ds + ((4 * kTcAPlane) >> 4);
+        const uint64_t b2 = ds + ((4 * kTcAPlane + kTcBPlane) >> 4);
         const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-        tc_mma_tf32(tm, da[0][s], db[0][s], id128, acc);  // Xr hi [B1 hi | B1 lo]
-        tc_mma_tf32(tm, da[1][s], db[0][s], id64, 1u);    // Xr lo B1 hi
-        tc_mma_tf32(tm, da[2][s], db[1][s], id128, 1u);   // Xi hi [B2 hi | B2 lo]
-        tc_mma_tf32(tm, da[3][s], db[1][s], id64, 1u);    // Xi lo B2 hi
+        tc_mma_tf32(tm, xrh, b1, id128, acc);  // Xr hi [B1 hi | B1 lo]
+        tc_mma_tf32(tm, xrl, b1, id64, 1u);    // Xr lo B1 hi
+        tc_mma_tf32(tm, xih, b2, id128, 1u);   // Xi hi [B2 hi | B2 lo]
+        tc_mma_tf32(tm, xil, b2, id64, 1u);    // Xi lo B2 hi
       }
-      tc_commit(&mbar);
+      tc_commit(&mbar[b]);
+    }
+    stage(c + 2);  // this chunk's staging buffer has been split
+  }
+  {  // the last chunk's commit covers every MMA issued before it
+    const int b = (nch - 1) & 1;
+    const bool ok = mbar_wait_bounded(&mbar[b], (ph >> b) & 1u, kLimit);
+    ph ^= 1u << b;
+    if (__syncthreads_or(!ok)) {
+      fail(!ok, b);
+      return;
     }
   }
-  const bool ok = mbar_wait_bounded(&mbar, phase, kLimit);  // the last chunk's MMAs
-  if (__syncthreads_or(!ok)) {
-    if (tid == 0) atomicExch(err, 1);
-    if (!ok) mbar_wait_bounded(&mbar, phase, kLimit);
-    tc_fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tm, 128);
-    return;
-  }
+  cp_async_wait<0>();
   tc_fence_after_sync();
   {  // T -> shared memory: warps 0-3 Re T, 4-7 Im T of row 32 (warp % 4) + lane,
      // each the sum of the hi-hi + lo-hi and the hi-lo accumulator halves
@@ -565,8 +623,8 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   // this block's E_r columns: Er[k1][r] = root[(u_s (U s_y + k1 - K/2)) mod UW]
   for (int t = tid; t < K * kTcRows; t += blockDim.x) {
     const int k1 = t / kTcRows, r = t - k1 * kTcRows, u = u0 + r;
-    const int b = modp32(U * sy + k1 - half, UW);
-    Er[t] = r < nrows ? roots[modp32((u < W / 2 ? u : u - W) * b, UW)] : make_float2(0.f, 0.f);
+    const int bk = modp32(U * sy + k1 - half, UW);
+    Er[t] = r < nrows ? roots[modp32((u < W / 2 ? u : u - W) * bk, UW)] : make_float2(0.f, 0.f);
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -597,6 +655,18 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
     if (y1) dst[(k1 + 1) * K + k2] = c10;
     if (y1 && x1) dst[(k1 + 1) * K + k2 + 1] = c11;
   }
+  // the last of the patch's CTAs to finish adds the shares (block order) and
+  // takes the argmax; done[lp] counts the finished CTAs and is left at zero
+  __shared__ int s_last;
+  __threadfence();  // this CTA's share is visible before it is counted
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&done[lp], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (tid == 0) done[lp] = 0;
+    updft_finish(lp, ids[lp], sy, sx, gridDim.x, U, K, part, shift, gap, rv, ri);
+  }
 }
 
 __global__ void __launch_bounds__(256)
@@ -608,42 +678,10 @@ k_updft_final(const int* __restrict__ ids, int W, int nblocks, int nparts,
   __shared__ int ri[32];
   pdl_trigger();
   pdl_wait();  // the partial sums come from updft_part
-  const int lp = blockIdx.x, j = ids[lp];
+  const int lp = blockIdx.x;
   int sy, sx;
   coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);
-  const int half = K / 2;
-  float best = -1.f, second = -1.f;
-  int bi = 0x7fffffff;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int b = 0; b < nblocks; ++b)
-      acc = cadd(acc, part[((size_t)lp * nblocks + b) * K * K + e]);  // fixed order
-    const float m = cabs2(acc);
-    if (m > best) {
-      second = fmaxf(second, best);
-      best = m;
-      bi = e;
-    } else {
-      second = fmaxf(second, m);
-    }
-  }
-  float gb = best;
-  int gbi = bi;
-  block_best(gb, gbi, rv, ri);
-  float s2 = (bi == gbi) ? second : best;  // best of this thread that is not the winner
-  __syncthreads();
-  {
-    int dummy = 0;
-    block_best(s2, dummy, rv, ri);
-  }
-  if (threadIdx.x == 0) {
-    const int k1 = gbi / K, k2 = gbi % K;
-    const float y = (float)sy + (float)(k1 - half) / (float)U;
-    const float x = (float)sx + (float)(k2 - half) / (float)U;
-    shift[2 * j] = -y;
-    shift[2 * j + 1] = -x;
-    gap[j] = gb > 0.f ? (gb - fmaxf(s2, 0.f)) / gb : 0.f;
-  }
+  updft_finish(lp, ids[lp], sy, sx, nblocks, U, K, part, shift, gap, rv, ri);
 }
 
 // U <= 1: the coarse peak alone.
@@ -802,7 +840,8 @@ cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, i
 
 cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const int* ids,
                          int npatch, const float* cval, const int* cidx, const float2* roots,
-                         float2* part, float* shift, float* gap, int* err, cudaStream_t s) {
+                         float2* part, float* shift, float* gap, int* done, int* err,
+                         cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   const int nparts = g.W / g.RX;
   if (g.U <= 1) {
@@ -811,11 +850,12 @@ cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const
   }
   const int nblocks = g.tc ? (g.W + kTcRows - 1) / kTcRows : g.W / g.RB;
   cudaError_t e = cudaSuccess;
-  if (g.tc) {
+  if (g.tc) {  // the shares are added by the last CTA of each patch
     const size_t sm = (size_t)kTcFixed + (size_t)g.U * g.W * sizeof(float2);
     PTY_DISPATCH_W(g.W, e = launch_pdl(k_updft_tc<WW>, dim3(nblocks, npatch), dim3(256), sm, s,
                                        scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K,
-                                       part, err));
+                                       part, ids, done, shift, gap, err));
+    return e;
   } else {
     PTY_DISPATCH_W(g.W, e = launch_pdl(k_updft_part<WW>, dim3(nblocks, npatch), dim3(512), g.smU,
                                        s, scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K,

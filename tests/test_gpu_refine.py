@@ -274,3 +274,20 @@ def test_tensor_core_registration_matches_fp32_cores_and_oracle(W, M):
     # the object update itself does not depend on the registration
     np.testing.assert_array_equal(O_tc, O_32)
     assert rel_l2(O_tc, st2.O) <= 1e-5
+
+
+def test_positions_clamped_at_the_object_border():
+    """A supplied position on the object's border with a large Adam step (lr
+    3 px) is clamped so that its crop stays inside, on both sides."""
+    wl = synth.tiny(W=64, M=1, ny=3, nx=3, step=12.0, seed=37, photons=1e6, jitter=1.0, err=2.0)
+    d = build(wl)
+    d["pos"][0] = [0.0, 0.0]
+    d["pos"][-1] = [wl.Hy - wl.W, wl.Hx - wl.W]
+    prob, st, pg, po, rg, ro = pair(wl, d, lr=3.0, start=1)
+    step_both(prob, st, d, pg, po, rg, ro)
+    for _ in range(3):
+        load_state(prob, st)
+        _, _, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+        compare_step(prob, st, sh, gaps)
+        pos = prob.positions(False)
+        assert pos.min() >= 0.0 and pos[:, 0].max() <= wl.Hy - wl.W and pos[:, 1].max() <= wl.Hx - wl.W

@@ -196,6 +196,20 @@ def test_edge_cases_single_position_corner_and_dark_pattern():
     check_one_iteration(wl, d, update_probe=False)
 
 
+def test_saturated_counts_and_zero_iterations():
+    """Counts clipped at the uint16 maximum take the same path on both sides
+    (no mask), and a call for zero iterations changes nothing."""
+    from paper_2205_04295_b300 import pty
+    wl = synth.tiny(W=64, M=2, ny=3, nx=3, step=10.0, seed=18, photons=1e6)
+    d = build(wl)
+    d["I"][2, 20:44, 20:44] = 65535
+    prob = gpu_problem(wl, d)
+    prob.run(0, pty.rpie_params())
+    np.testing.assert_array_equal(prob.object(False), d["O0"])
+    np.testing.assert_array_equal(prob.probe(False), d["P0"])
+    check_one_iteration(wl, d)
+
+
 def test_dark_pattern_with_probe_update_stays_finite():
     # A dark pattern alone in its group drives an ePIE-like probe step
     # (beta = 1) to exactly zero in FP32; zero denominators skip the update
