@@ -84,3 +84,14 @@ def test_init_without_gpu_fails_cleanly():
     assert rc != pty.PTY_OK and not h.value
     d.W = 100
     assert pty.lib().pty_init_problem(ctypes.byref(d), ctypes.byref(h)) == pty.PTY_EINVAL
+
+
+def test_unknown_problem_flags_are_rejected_before_any_device_call():
+    """pty_problem_desc.flags accepts PTY_FLAG_FP32_REGISTRATION only; any other
+    bit fails with PTY_EINVAL during argument checking (no GPU needed)."""
+    L = pty.lib()
+    d = pty.ProblemDesc(64, 2, 4, 100, 100, None, pty.ALLOC_FN(), pty.FREE_FN(), None, 0, 4)
+    h = ctypes.c_void_p()
+    assert L.pty_init_problem(ctypes.byref(d), ctypes.byref(h)) == pty.PTY_EINVAL
+    assert b"unknown flags" in L.pty_last_error()
+    assert not h.value

@@ -291,3 +291,19 @@ def test_positions_clamped_at_the_object_border():
         compare_step(prob, st, sh, gaps)
         pos = prob.positions(False)
         assert pos.min() >= 0.0 and pos[:, 0].max() <= wl.Hy - wl.W and pos[:, 1].max() <= wl.Hx - wl.W
+
+
+def test_fine_grid_beyond_the_tensor_core_tile_falls_back():
+    """U = 25 gives K = 38 fine-grid points per axis, more than the tensor-core
+    kernel's 32-column tile: the FP32-core kernel takes it, with the same
+    parity as at U = 20."""
+    wl = synth.tiny(W=64, M=2, ny=4, nx=4, step=10.0, seed=38, photons=1e6, jitter=1.0, err=2.0)
+    d = build(wl)
+    prob, st, pg, po, rg, ro = pair(wl, d, U=25, start=1)
+    step_both(prob, st, d, pg, po, rg, ro)
+    for _ in range(2):
+        load_state(prob, st)
+        _, _, sh, gaps = step_both(prob, st, d, pg, po, rg, ro)
+        flip = compare_step(prob, st, sh, gaps)
+        assert flip.sum() <= 1
+        assert rel_l2(prob.object(False), st.O) <= 1e-5
