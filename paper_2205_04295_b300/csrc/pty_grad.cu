@@ -30,6 +30,17 @@ PTY_D float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Barrier over a row line's L lanes: consecutive threads, so where lines tile
+// warps (L = 8, 16) the warp suffices (every thread of the warp calls it);
+// L = 12 lines straddle warps and take the CTA barrier.
+template <int W>
+PTY_D void grad_line_sync() {
+  if constexpr (32 % Line<W>::L == 0)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
 struct Bil {
   int iy, ix;
   float fy, fx;
@@ -132,7 +143,7 @@ k_grad_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__
       }
       fwd_step1<W>(v, lane, tw, lbuf);
     }
-    __syncthreads();
+    grad_line_sync<W>();  // the transpose stays within the line
     if (act && lane < G::N1) {
       float2 z[G::N2];
       fwd_step3<W>(z, lane, lbuf);
