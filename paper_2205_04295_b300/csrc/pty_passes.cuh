@@ -52,13 +52,25 @@ PTY_D float block_max(float v, float* red) {
 }
 
 // ---------------------------------------------------------------- pass A
-// Request (cp.async) the crop rows [r0, r0 + R) of patch slot lp into `ost`.
+// Request (cp.async) the crop rows [r0, r0 + R) of the patch with corner cc
+// into `ost` (R x W, 16-byte aligned).  A crop row that starts on a 16-byte
+// boundary moves in 16-byte pieces, any other (an odd corner column) in
+// 8-byte pieces.
+template <int W>
+PTY_D void stage_crop_rows(const float2* O, int Hx, int2 cc, int R, int r0, float2* ost) {
+  for (int r = 0; r < R; ++r) {
+    const float2* src = O + (size_t)(cc.x + r0 + r) * Hx + cc.y;
+    float2* dst = ost + r * W;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+      for (int h = threadIdx.x; h < W / 2; h += blockDim.x) cp_async<16>(dst + 2 * h, src + 2 * h);
+    } else {
+      for (int c = threadIdx.x; c < W; c += blockDim.x) cp_async<8>(dst + c, src + c);
+    }
+  }
+}
 template <int W>
 PTY_D void rows_fwd_stage(const float2* O, int Hx, int2 cc, int R, int r0, float2* ost) {
-  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
-    const int r = e / W, c = e - r * W;
-    cp_async<8>(ost + e, O + (size_t)(cc.x + r0 + r) * Hx + cc.y + c);
-  }
+  stage_crop_rows<W>(O, Hx, cc, R, r0, ost);
 }
 
 // Barrier over a row line's L lanes: they are consecutive threads, so where
@@ -422,10 +434,7 @@ PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 c
                    scratch + (((size_t)lp * npl + k) * W + r0 + r) * W + 2 * h);
     }
   }
-  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
-    const int r = e / W, c = e - r * W;
-    cp_async<8>(ost + e, O + (size_t)(cc.x + r0 + r) * Hx + cc.y + c);
-  }
+  stage_crop_rows<W>(O, Hx, cc, R, r0, ost);
 }
 
 // The next patch's far-field and crop rows are requested while the current
