@@ -33,7 +33,10 @@ def candidates(W, M):
     L = LANES[W]
     Rs = [r for r in _pow2(1, 16) if W % r == 0 and M * r * L <= 256]
     CBs = [c for c in _pow2(2, 16) if (W // 2) % c == 0 and M * c * L <= 384]
-    return Rs, [1, 2, 4, 8, 16], CBs, [48 << 20, 96 << 20, 144 << 20, 192 << 20], [1, 2, 4]
+    # patches per CTA: not only powers of two, so that a group's grid can end
+    # on a nearly full wave of CTAs
+    return (Rs, [1, 2, 3, 4, 5, 6, 8, 10, 12, 16], CBs, [48 << 20, 96 << 20, 144 << 20, 192 << 20],
+            [1, 2, 3, 4])
 
 
 def time_iteration(prob, params, reps=2):
