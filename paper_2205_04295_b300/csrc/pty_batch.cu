@@ -149,7 +149,7 @@ k_batch(const BatchProb* __restrict__ probs, const BatchTask* __restrict__ tasks
 size_t batch_smem(const Tiling& t) {
   // the batched column pass reads straight into registers: no stage
   const size_t smB = t.smB - (size_t)t.M * t.W * t.CB * sizeof(float2);
-  return std::max({t.smA, smB, t.smC, (size_t)256 * sizeof(double)});  // 256: the error reduction
+  return std::max({t.smA_staged, smB, t.smC, (size_t)256 * sizeof(double)});  // 256: the error reduction
 }
 
 cudaError_t batch_grid(size_t smem, int* ctas) {

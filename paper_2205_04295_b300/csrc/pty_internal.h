@@ -26,6 +26,7 @@ struct Tiling {
   int ppcb;      // patches per CTA, column pass
   int thrA, thrB, thrC;
   size_t smA, smB, smC, smI;  // dynamic shared memory (bytes)
+  size_t smA_staged;          // pass A with its probe rows in shared memory (batched form)
   int n_pmax;    // CTAs of the probe-apply kernel (= partial maxima)
   int pstage;    // 1: pass C copies its probe rows to shared memory (when that
                  // costs it no CTA per SM), 0: reads them through L1 at use

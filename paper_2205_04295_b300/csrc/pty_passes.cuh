@@ -89,8 +89,11 @@ PTY_D void line_sync() {
 }
 
 // The next patch's crop rows are requested while the current patch is
-// transformed (double-buffered in shared memory).
-template <int W>
+// transformed (double-buffered in shared memory).  PSTAGE copies the CTA's
+// probe rows to shared memory once; without it they are read at use through
+// L1 (a few KB per CTA, cached), which leaves that shared memory free for more
+// CTAs per SM.
+template <int W, bool PSTAGE = true>
 PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
            int M, int R, int ppc, const int* __restrict__ ids,
            const int2* __restrict__ corners, int npatch,
@@ -99,8 +102,8 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
-  float2* Prow = tw + W;
-  float2* tbuf = Prow + M * R * W;
+  float2* Prow = tw + W;                       // M x R x W probe rows (PSTAGE)
+  float2* tbuf = Prow + (PSTAGE ? M * R * W : 0);
   float2* ost = tbuf + (M + xo) * R * G::LP;  // 2 x R x W crop rows
   int2* scor = reinterpret_cast<int2*>(ost + 2 * R * W);  // ppc corners
 
@@ -118,9 +121,11 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
   __syncthreads();
   if (p0 < p1) rows_fwd_stage<W>(O, Hx, scor[0], R, r0, ost);
   cp_async_commit();
-  for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
-    const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
-    Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
+  if constexpr (PSTAGE) {
+    for (int e = threadIdx.x; e < M * R * W; e += blockDim.x) {
+      const int k = e / (R * W), rem = e - k * R * W, r = rem / W, c = rem - r * W;
+      Prow[e] = P[((size_t)k * W + r0 + r) * W + c];
+    }
   }
 
   // lines: (mode k, row r) for k < M, and with xo the crop itself as plane M
@@ -136,14 +141,15 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
     cp_async_commit();
     float omax = 0.f;
     if (act && lane < G::N2) {
-      const float2* prow = Prow + (k * R + r) * W;
+      const float2* prow = PSTAGE ? Prow + (k * R + r) * W
+                                  : P + ((size_t)(k < M ? k : 0) * W + r0 + r) * W;
       const float2* orow = ost + ((lp - p0) & 1) * R * W + r * W;
       float2 v[G::N1];
 #pragma unroll
       for (int n1 = 0; n1 < G::N1; ++n1) {
         const int c = G::N2 * n1 + lane;
         const float2 o = orow[c];
-        v[n1] = k < M ? cmul(prow[c], o) : o;
+        v[n1] = k < M ? cmul(PSTAGE ? prow[c] : __ldg(prow + c), o) : o;
         omax = fmaxf(omax, cabs2(o));
       }
       fwd_step1<W>(v, lane, tw, lbuf);

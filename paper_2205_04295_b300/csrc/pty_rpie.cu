@@ -21,7 +21,8 @@ k_rows_fwd(const float2* __restrict__ O, int Hx, const float2* __restrict__ P,
            const int2* __restrict__ corners, int npatch,
            const float2* __restrict__ tw_g, float2* __restrict__ scratch,
            float* __restrict__ omax_part, int npl, int xo) {
-  rows_fwd_body<W>(O, Hx, P, M, R, ppc, ids, corners, npatch, tw_g, scratch, omax_part, npl, xo, blockIdx.x, blockIdx.y);
+  rows_fwd_body<W, false>(O, Hx, P, M, R, ppc, ids, corners, npatch, tw_g, scratch, omax_part, npl,
+                          xo, blockIdx.x, blockIdx.y);
 }
 
 // Two CTAs per SM.  BIG launches up to 384 threads and holds 80 registers a
@@ -335,7 +336,7 @@ bool encode_far_field_map(const void* base, int W, size_t planes, int CB, CUtens
 
 bool tiling_fits(const Tiling& t) {
   const size_t lim = (size_t)smem_optin() - 1024;
-  return t.thrA <= 256 && t.thrB <= 384 && t.thrC <= 256 && t.smA <= lim && t.smB <= lim &&
+  return t.thrA <= 256 && t.thrB <= 384 && t.thrC <= 256 && t.smA_staged <= lim && t.smB <= lim &&
          t.smC <= lim;
 }
 
@@ -422,7 +423,10 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   t.thrA = round32(MA * R * L);
   t.thrC = round32(M * R * L);
   t.thrB = round32(M * CB * L);
-  t.smA = (size_t)(W + M * R * W + MA * R * LP + 2 * R * W + t.ppc) * sizeof(float2);
+  // the per-pass kernel reads its probe rows through L1; the batched form's
+  // task function stages them (smA_staged)
+  t.smA = (size_t)(W + MA * R * LP + 2 * R * W + t.ppc) * sizeof(float2);
+  t.smA_staged = t.smA + (size_t)M * R * W * sizeof(float2);
   // pass B transforms the M modes only (the crop plane's column DFTs are
   // taken by the registration's correlation pass)
   t.smB = (size_t)(W + M * W * CB + M * CB * LP) * sizeof(float2) +
