@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define PTY_ABI_VERSION 2
+#define PTY_ABI_VERSION 3
 
 enum {
   PTY_OK = 0,
@@ -193,13 +193,23 @@ int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t,
  * patches per CTA of the row passes, CB columns per CTA of the column pass
  * (2, 4, 8 or 16, dividing W/2; M * CB * lanes <= 384 threads), scratch_bytes
  * the far-field chunk budget,
- * ppcb patches per CTA of the column pass.  Results do not depend on the
- * tiling except through the summation order of the probe sums.  The
- * project's autotuner (paper_2205_04295_b300/autotune.py) searches these. */
+ * ppcb patches per CTA of the column pass.
+ * fused = S > 0 (W <= 128 only) replaces the three passes of the M-rPIE
+ * section's per-patch update (Eqs. 1, 2, 4-7) by one kernel per group: a
+ * thread-block cluster of M x S CTAs per patch (M * S <= 8; S = 1, 2, 4 or
+ * 8, with W / S a multiple of both DFT factors of W), each CTA holding W / S
+ * rows of one mode's W x W plane in shared memory, so that a patch makes one
+ * trip to global memory (no far-field scratch); PTY_EINVAL where that form
+ * does not fit.  Registration (pty_refine_positions) runs on it too; the
+ * differentiable form and the batched form keep their own kernels.  Results
+ * do not depend on the tiling except through the summation order of the
+ * probe sums.  The project's autotuner (paper_2205_04295_b300/autotune.py)
+ * searches these. */
 typedef struct {
   int R, ppc, CB;
   size_t scratch_bytes;
   int ppcb;         /* patches per CTA of the column pass (0 = default) */
+  int fused;        /* slabs per mode of the fused patch kernel (0 = three passes) */
 } pty_tiling;
 int pty_set_tiling(pty_handle* h, const pty_tiling* t);
 int pty_get_tiling(pty_handle* h, pty_tiling* t);
@@ -210,7 +220,7 @@ int pty_get_tiling(pty_handle* h, pty_tiling* t);
  * the totals since the last reset and, if reset != 0, zeroes them. */
 enum { PTY_K_ROWS_FWD = 0, PTY_K_COLS = 1, PTY_K_ROWS_INV = 2, PTY_K_PROBE = 3,
        PTY_K_REDUCE = 4, PTY_K_REFINE = 5, PTY_K_GRAD = 6, PTY_K_OTHER = 7,
-       PTY_K_COUNT = 8 };
+       PTY_K_PATCH = 8, PTY_K_COUNT = 9 };
 typedef struct {
   long long launches[PTY_K_COUNT];  /* kernel launches per kind */
   double ms[PTY_K_COUNT];           /* summed device time per kind (mode 1) */

@@ -238,6 +238,7 @@ struct pty_handle {
   int flags = 0;             // PTY_FLAG_* of the problem description
   pty::Tiling tl{}, tlr{};   // plain and refining launch geometry
   int Qc = 1, Qcr = 1, nslots = 1;
+  pty::PatchGeo pg{};        // fused patch kernel (pg.S > 0: it replaces the three passes)
   pty::RefGeo rg{};
   float2* roots = nullptr;
   float2* upart = nullptr;  // fine-grid partial sums of the registration
@@ -468,7 +469,60 @@ pty::UpdArgs upd_args(const pty_rpie_params* p) {
 }
 
 // refine: 0 = plain, 1 = XCORR_A, 2 = XCORR_B registration of every patch
+// One group on the fused patch kernel: without registration the whole group
+// in one launch (no scratch), with it in chunks of the registration's scratch
+// planes, each chunk followed by the registration kernels.
+int run_group_fused(pty_handle* h, int g, const pty_rpie_params* p, int refine) {
+  const int n = h->gptr[g + 1] - h->gptr[g];
+  const int* ids = h->gpos_d + h->gptr[g];
+  const pty::Tiling& tl = refine ? h->tlr : h->tl;
+  const int Qc = refine ? h->Qcr : n;
+  pty::PatchArgs a = {};
+  a.O = h->O; a.Hx = h->Hx; a.M = h->M; a.P = h->P; a.I = h->I; a.corners = h->corners;
+  a.tw = h->tw; a.inv_w = h->inv_w; a.a = upd_args(p);
+  a.pmax_part = h->pmax_part; a.n_pmax = h->tl.n_pmax;
+  a.pnum = h->pnum; a.pden = h->pden; a.osum = h->osum;
+  a.err_part = h->err_part; a.nb = h->W / tl.CB;  // the stride the error reduction reads
+  a.scratch = h->scratch; a.npl = tl.npl; a.refine = refine;
+  int used = 0;
+  for (int c0 = 0; c0 < n; c0 += Qc) {
+    const int nc = std::min(Qc, n - c0);
+    const int* idc = ids + c0;
+    a.ids = idc;
+    a.npatch = nc;
+    a.accumulate = c0 > 0;
+    const int ncl = std::min(h->pg.ncap, nc);
+    used = std::max(used, ncl);
+    {
+      pty_handle::Mark m(h, PTY_K_PATCH);
+      CU(pty::launch_patch(h->pg, a, ncl, h->stream));
+    }
+    if (refine) {
+      pty_handle::Mark m(h, PTY_K_REFINE);
+      if (refine == 2) {
+        CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
+        h->n_launch[PTY_K_REFINE] += 1;
+      }
+      CU(pty::launch_xcorr_cols(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
+      CU(pty::launch_xcorr_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->cval, h->cidx,
+                                h->stream));
+      CU(pty::launch_updft(h->rg, h->scratch, tl.npl, h->M, idc, nc, h->cval, h->cidx,
+                           h->roots, h->upart, h->shift, h->gap, h->updone, h->tma_err,
+                           h->stream));
+      h->n_launch[PTY_K_REFINE] += 2;
+    }
+  }
+  if (p->update_probe) {
+    pty_handle::Mark m(h, PTY_K_PROBE);
+    CU(pty::launch_probe_apply(h->tl, h->P, h->pnum, h->pden, h->osum, used, p->alpha_P,
+                               p->reg_eps, h->pmax_part, h->stream));
+  }
+  h->patches += n;
+  return PTY_OK;
+}
+
 int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0) {
+  if (h->pg.S > 0) return run_group_fused(h, g, p, refine);
   const int n = h->gptr[g + 1] - h->gptr[g];
   const int* ids = h->gpos_d + h->gptr[g];
   const pty::UpdArgs a = upd_args(p);
@@ -1315,6 +1369,15 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
     return fail(PTY_EINVAL, "columns per CTA CB=%d invalid for W=%d, M=%d", t->CB, W, M);
   if (t->ppc < 0 || t->ppc > 64) return fail(PTY_EINVAL, "patches per CTA %d", t->ppc);
   if (t->ppcb < 0 || t->ppcb > 64) return fail(PTY_EINVAL, "column patches per CTA %d", t->ppcb);
+  pty::PatchGeo npg{};
+  if (t->fused) {
+    if (t->fused < 0 || t->fused > 8 || !pow2(t->fused))
+      return fail(PTY_EINVAL, "fused slabs per mode S=%d: 1, 2, 4 or 8", t->fused);
+    npg = pty::make_patch_geo(W, M, t->fused);
+    if (npg.ncap < 1)
+      return fail(PTY_EINVAL, "the fused patch kernel does not fit W=%d, M=%d, S=%d", W, M,
+                  t->fused);
+  }
   pty::Tiling nt = pty::make_tiling(W, M, false, 512, t->R, t->ppc, t->CB);
   if (t->ppcb > 0) nt.ppcb = t->ppcb;
   if (!pty::tiling_fits(nt)) return fail(PTY_EINVAL, "tiling exceeds the per-CTA limits");
@@ -1337,7 +1400,8 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   // grow the buffers whose size depends on the tiling
   // slots for this ppc and for the default ppc (4) the batched form uses
   const int ppc_min = std::min(std::min(nt.ppc, nr.ppc), 4);
-  const int nslots = (std::max(std::max(Qc, Qcr), h->Qcg) + ppc_min - 1) / ppc_min;
+  const int nslots = std::max((std::max(std::max(Qc, Qcr), h->Qcg) + ppc_min - 1) / ppc_min,
+                              npg.ncap);  // the fused kernel: one slot per cluster
   const size_t scratch = std::max(std::max((size_t)Qc * M, (size_t)Qcr * nr.npl),
                                   (size_t)h->Qcg * (M + 1)) * W2;
   const size_t cur_scratch = std::max(std::max((size_t)h->Qc * M, (size_t)h->Qcr * h->tlr.npl),
@@ -1375,6 +1439,7 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   TRY(alloc_into(h, h->omax_part, std::max(omax_need, (size_t)std::max(Qc, Qcr) * W)));
   h->tl = nt;
   h->tlr = nr;
+  h->pg = npg;
   remap_scratch(h);
   h->Qc = Qc;
   h->Qcr = Qcr;
@@ -1394,6 +1459,7 @@ int pty_get_tiling(pty_handle* h, pty_tiling* t) {
   t->CB = h->tl.CB;
   t->scratch_bytes = (size_t)h->Qc * h->M * h->W * h->W * sizeof(float2);
   t->ppcb = h->tl.ppcb;
+  t->fused = h->pg.S > 0 ? h->pg.S : 0;
   return PTY_OK;
 }
 

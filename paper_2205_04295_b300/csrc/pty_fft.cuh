@@ -48,9 +48,11 @@ template <bool INV> PTY_D float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 // multiply by exp(-i t) (forward) or exp(+i t) (inverse), c = cos t, s = sin t
+// (the fused multiply-adds are written out, so that every kernel rounds the
+// same way whatever the compiler would contract)
 template <bool INV> PTY_D float2 rot(float2 a, float c, float s) {
-  return INV ? make_float2(a.x * c - a.y * s, a.x * s + a.y * c)
-             : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
+  return INV ? make_float2(fmaf(a.x, c, -(a.y * s)), fmaf(a.x, s, a.y * c))
+             : make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -(a.x * s)));
 }
 // multiply by table twiddle w (forward) or conj(w) (inverse)
 template <bool INV> PTY_D float2 twiddle(float2 a, float2 w) {
@@ -76,10 +78,10 @@ template <bool INV> struct Dft<3, INV> {
   static PTY_D void run(float2* v) {
     float2 t = cadd(v[1], v[2]);
     float2 m = make_float2(fmaf(-0.5f, t.x, v[0].x), fmaf(-0.5f, t.y, v[0].y));
-    float2 r = cscale(mul_mi<INV>(csub(v[1], v[2])), kS3);
+    float2 r = mul_mi<INV>(csub(v[1], v[2]));
     v[0] = cadd(v[0], t);
-    v[1] = cadd(m, r);
-    v[2] = csub(m, r);
+    v[1] = make_float2(fmaf(kS3, r.x, m.x), fmaf(kS3, r.y, m.y));
+    v[2] = make_float2(fmaf(-kS3, r.x, m.x), fmaf(-kS3, r.y, m.y));
   }
 };
 

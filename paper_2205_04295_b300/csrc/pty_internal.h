@@ -204,6 +204,48 @@ cudaError_t launch_batch(const BatchProb* probs, const BatchTask* tasks, int nta
                          unsigned long long timeout_ns, int ctas, size_t smem,
                          cudaStream_t s);
 
+// ---- fused single-kernel patch path for W <= 128 (pty_patch.cu) ----------
+// One cluster of M x S CTAs per patch: CTA (mode k, slab s) holds rows
+// [s W/S, (s+1) W/S) of mode k's W x W plane in shared memory; the 2-D DFTs,
+// the modulus constraint and the object / probe-sum updates run there, with
+// the column lines and the cross-mode sums reaching the other slabs through
+// distributed shared memory.  The far-field scratch is written only for the
+// registration's crop planes.
+struct PatchGeo {
+  int W, M, S;     // S slabs per mode (1, 2, 4, 8); cluster M * S <= 8
+  int NL, NT;      // lines per round and threads per CTA
+  size_t sm;       // dynamic shared memory (bytes)
+  int ncap;        // clusters resident at once (0: the launch cannot run)
+};
+struct PatchArgs {
+  float2* O;
+  int Hx, M;
+  const float2* P;
+  const uint16_t* I;
+  const int* ids;
+  const int2* corners;
+  int npatch, NL;
+  const float2* tw;
+  float inv_w;
+  UpdArgs a;
+  const float* pmax_part;
+  int n_pmax;
+  float2* pnum;
+  float* pden;
+  float* osum;
+  int accumulate;   // add to the probe sums of the slots (a later chunk)
+  float* err_part;
+  int nb;           // error partial slots per pattern (the first gets the sum)
+  float2* scratch;
+  int npl;
+  int refine;       // 0; 1: XCORR_A crop planes M, M + 1; 2: XCORR_B planes M, M + 1
+};
+// S = 0 or an unsupported (W, M, S): ncap = 0.  Queries the device.
+PatchGeo make_patch_geo(int W, int M, int S);
+cudaError_t set_patch_smem(int W);
+// nclusters <= ncap clusters over a.npatch patches; slot c = cluster c.
+cudaError_t launch_patch(const PatchGeo& g, const PatchArgs& a, int nclusters, cudaStream_t s);
+
 cudaError_t launch_fft2(void* data, int W, int batch, int inverse,
                         const float2* tw, cudaStream_t s);
 cudaError_t launch_finite_check(const float* p, size_t n, int* flag,

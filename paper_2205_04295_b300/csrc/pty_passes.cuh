@@ -364,11 +364,13 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
         for (int kk = 0; kk < M; ++kk) s += Sb[(kk * W + u) * CB + cl];
         const float sI = sqrt_rs((float)cn[el]);
         if (!GRAD) {
-          const float a = sqrt_rs(s) * inv_w;
-          const float d = a - sI;
+          // rounded products and sums written out (no contraction), as in
+          // the fused patch kernel
+          const float a = __fmul_rn(sqrt_rs(s), inv_w);
+          const float d = __fsub_rn(a, sI);
           e = fmaf(d, d, e);
           // quotient by a reciprocal-multiply (within 2 ulp of the division)
-          Sb[u * CB + cl] = __fdividef(sI, a + eps) * f2;
+          Sb[u * CB + cl] = __fmul_rn(__fdividef(sI, __fadd_rn(a, eps)), f2);
           if (xb >= 0) {
             // XCORR_B: the model intensity and the counts, unshifted, as the
             // real parts of scratch planes xb and xb + 1
@@ -502,7 +504,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   __syncthreads();
   {
     const float pmax = s_pmax;
-    const float gden = a.gamma * pmax + a.reg_eps * pmax;
+    const float gden = fmaf(a.gamma, pmax, a.reg_eps * pmax);  // one rounding, as in every kernel
     for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
       const int rr = e / W, c = e - rr * W;
       float s = 0.f;

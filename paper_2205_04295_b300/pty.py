@@ -48,11 +48,11 @@ class RefineParams(ctypes.Structure):
                 ("point", c_int)]
 
 
-K_NAMES = ["rows_fwd", "cols", "rows_inv", "probe", "reduce", "refine", "grad", "other"]
+K_NAMES = ["rows_fwd", "cols", "rows_inv", "probe", "reduce", "refine", "grad", "other", "patch"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8),
+    _fields_ = [("launches", ctypes.c_longlong * 9), ("ms", ctypes.c_double * 9),
                 ("patches", ctypes.c_longlong)]
 
     def as_dict(self):
@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
 
 class Tiling(ctypes.Structure):
     _fields_ = [("R", c_int), ("ppc", c_int), ("CB", c_int), ("scratch_bytes", c_size_t),
-                ("ppcb", c_int)]
+                ("ppcb", c_int), ("fused", c_int)]
 
 
 class BatchSchedule(ctypes.Structure):
@@ -462,14 +462,17 @@ class Problem:
         check(lib().pty_orthogonalize_probe(self.h, w.ctypes.data))
         return w
 
-    def set_tiling(self, R=0, ppc=0, CB=0, scratch_bytes=0, ppcb=0):
-        check(lib().pty_set_tiling(self.h, ctypes.byref(Tiling(R, ppc, CB, scratch_bytes, ppcb))))
+    def set_tiling(self, R=0, ppc=0, CB=0, scratch_bytes=0, ppcb=0, fused=0):
+        """fused = S > 0: the single-kernel patch path (W <= 128), a cluster
+        of M x S CTAs per patch; 0: the three passes."""
+        check(lib().pty_set_tiling(self.h, ctypes.byref(Tiling(R, ppc, CB, scratch_bytes, ppcb,
+                                                               fused))))
 
     def tiling(self):
         t = Tiling()
         check(lib().pty_get_tiling(self.h, ctypes.byref(t)))
         return {"R": t.R, "ppc": t.ppc, "CB": t.CB, "scratch_bytes": int(t.scratch_bytes),
-                "ppcb": t.ppcb}
+                "ppcb": t.ppcb, "fused": t.fused}
 
     def profile(self, mode):
         check(lib().pty_profile(self.h, int(mode)))

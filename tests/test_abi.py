@@ -25,7 +25,7 @@ def test_library_exports_every_declared_symbol():
     assert "pty_run_iterations" in names and "pty_init_problem" in names
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
-    assert L.pty_abi_version() == 2
+    assert L.pty_abi_version() == 3
 
 
 def _groups_equal(pos, W, max_group=0, order=None):
