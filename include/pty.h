@@ -196,11 +196,11 @@ int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t,
  * ppcb patches per CTA of the column pass.
  * fused = S > 0 (W <= 128 only) replaces the three passes of the M-rPIE
  * section's per-patch update (Eqs. 1, 2, 4-7) by one kernel per group: a
- * thread-block cluster of M x S CTAs per patch (M * S <= 8; S = 1, 2, 4 or
- * 8, with W / S a multiple of both DFT factors of W), each CTA holding W / S
- * rows of one mode's W x W plane in shared memory, so that a patch makes one
- * trip to global memory (no far-field scratch); PTY_EINVAL where that form
- * does not fit.  Registration (pty_refine_positions) runs on it too; the
+ * thread-block cluster of S CTAs per patch (S = 1, 2, 4 or 8, W / S a
+ * multiple of 8), each CTA holding W / S rows of every mode's W x W plane in
+ * shared memory and, between two transposes through distributed shared
+ * memory, W / S columns, so that a patch makes one trip to global memory
+ * (no far-field scratch); PTY_EINVAL where the slabs do not fit.  Registration (pty_refine_positions) runs on it too; the
  * differentiable form and the batched form keep their own kernels.  Results
  * do not depend on the tiling except through the summation order of the
  * probe sums.  The project's autotuner (paper_2205_04295_b300/autotune.py)

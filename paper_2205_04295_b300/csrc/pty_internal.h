@@ -205,14 +205,13 @@ cudaError_t launch_batch(const BatchProb* probs, const BatchTask* tasks, int nta
                          cudaStream_t s);
 
 // ---- fused single-kernel patch path for W <= 128 (pty_patch.cu) ----------
-// One cluster of M x S CTAs per patch: CTA (mode k, slab s) holds rows
-// [s W/S, (s+1) W/S) of mode k's W x W plane in shared memory; the 2-D DFTs,
-// the modulus constraint and the object / probe-sum updates run there, with
-// the column lines and the cross-mode sums reaching the other slabs through
-// distributed shared memory.  The far-field scratch is written only for the
-// registration's crop planes.
+// One cluster of S CTAs per patch: CTA s holds rows [s W/S, (s+1) W/S) of
+// every mode's W x W plane and, between two transposes through distributed
+// shared memory, columns [s W/S, (s+1) W/S); the 2-D DFTs, the modulus
+// constraint and the object / probe-sum updates run there.  The far-field
+// scratch is written only for the registration's crop planes.
 struct PatchGeo {
-  int W, M, S;     // S slabs per mode (1, 2, 4, 8); cluster M * S <= 8
+  int W, M, S;     // S CTAs per patch (1, 2, 4, 8; W / S a multiple of 8)
   int NL, NT;      // lines per round and threads per CTA
   size_t sm;       // dynamic shared memory (bytes)
   int ncap;        // clusters resident at once (0: the launch cannot run)

@@ -3,31 +3,34 @@
 // unitary far-field DFT Eq. 2, mixed-state modulus constraint Eq. 7, object
 // update Eq. 6 and the probe update's sums Eq. 5).
 //
-// One thread-block cluster of M x S CTAs works on one patch at a time; CTA
-// (mode k, slab s) keeps rows [s W/S, (s+1) W/S) of mode k's W x W plane in
-// shared memory for the whole patch:
+// One thread-block cluster of S CTAs works on one patch at a time.  CTA s
+// holds, for every mode, rows [s H, (s+1) H) of the W x W plane (H = W / S,
+// "row slab" RA) and, between the two transposes, columns [s H, (s+1) H)
+// ("column slab" CA, stored one column line per row of the buffer):
 //
-//   forward row DFTs of psi_k = P_k o_j on the slab's rows        (local)
-//   forward column DFTs over the S slabs of mode k, in place      (DSMEM)
-//   constraint: S = sum_k |Psi_k|^2, Psi_k *= sqrt(I)/(sqrt(S)+eps) on this
-//   CTA's share of the slab's pixels, for every mode              (DSMEM)
-//   inverse column DFTs, in place                                 (DSMEM)
-//   inverse row DFTs                                              (local)
-//   object update and probe sums on this CTA's share of the pixels,
-//   summing D_k conj(P_k) over the modes                          (DSMEM)
+//   forward row DFTs of psi_k = P_k o_j on the row slab           (local)
+//   gather: column slab from the S row slabs                      (DSMEM)
+//   forward column DFTs, modulus constraint S = sum_k |Psi_k|^2,
+//   Psi_k *= sqrt(I)/(sqrt(S)+eps), inverse column DFTs           (local)
+//   scatter: column slab back into the S row slabs                (DSMEM)
+//   inverse row DFTs, object update and probe sums                (local)
 //
-// so that a patch reads its crop, probe rows and counts and writes its crop
-// and probe sums once, with no far-field scratch (the registration's crop
-// planes excepted).  Every step repeats the three-pass path's arithmetic
-// (the same line DFTs, constraint and update expressions and summation
-// orders over the modes); the probe sums are grouped per cluster instead of
-// per CTA column.
+// Distributed shared memory moves about 15-20 bytes per clock per SM on
+// this part (a few times less than L2), so the only cross-CTA traffic is the
+// two transposes, 2 (S-1)/S of the patch's far field per CTA, read and
+// written in row segments; the sums over the modes never leave a CTA.  A
+// patch reads its crop, probe rows and counts and writes its crop and probe
+// sums once, with no far-field scratch (the registration's crop planes
+// excepted).  Every step repeats the three-pass path's arithmetic (the same
+// line DFTs, constraint and update expressions and summation orders over
+// the modes); the probe sums are grouped per cluster instead of per CTA
+// column.
 //
-// A CTA's share of a slab is the rows lr = k, k + M, ... of the slab (whole
-// rows, so that with XCORR_A it can also row-transform its rows of the
-// refined crop).  The cluster barrier separates the six phases; a CTA never
-// reads another's slab outside the phase that owns it, and the last barrier
-// keeps every CTA resident until no other one reads its slab.
+// Ordering: a CTA's row slab is read by the others only between the first
+// and the second cluster barrier of a patch (gather) and written by them
+// only between the second and the third (scatter); everything else is
+// local.  A patch's probe rows and counts are requested (cp.async) as soon as
+// its corner is known and used after the forward DFTs.
 #include "pty_cluster.cuh"
 #include "pty_passes.cuh"
 
@@ -41,37 +44,36 @@ constexpr int kPatchMaxThreads = 512;
 
 template <int W, int S>
 __host__ __device__ constexpr bool patch_ok() {
-  return W <= 128 && W % S == 0 && (W / S) % Line<W>::N1 == 0 && (W / S) % Line<W>::N2 == 0;
+  return W <= 128 && W % S == 0 && (W / S) % 8 == 0;  // 16-byte count pieces
 }
 
 template <int W, int S>
 __global__ void __launch_bounds__(kPatchMaxThreads, 1) k_patch(const __grid_constant__ PatchArgs q) {
   using G = Line<W>;
-  constexpr int HS = W / S;     // rows (and columns) of the slab
-  constexpr int PITCH = W + 1;  // odd row pitch: a column line's lanes hit distinct banks
-  static_assert(patch_ok<W, S>(), "a slab holds whole DFT sub-blocks of a column line");
+  constexpr int H = W / S;      // rows of the row slab, columns of the column slab
+  constexpr int PITCH = W + 1;  // odd line pitch: strided accesses hit distinct banks
+  static_assert(patch_ok<W, S>(), "slab width");
+  const int M = q.M, NL = q.NL;
   extern __shared__ float4 smem4[];
   float2* tw = reinterpret_cast<float2*>(smem4);
-  float2* A = tw + W;                    // HS x PITCH: this CTA's slab
-  float2* lbase = A + HS * PITCH;        // NL transpose lines
+  float2* RA = tw + W;                   // [k][r][c]: M x H lines of PITCH
+  float2* CA = RA + M * H * PITCH;       // [k][cl][u]: M x H column lines of PITCH
+  float2* lbase = CA + M * H * PITCH;    // NL transpose lines
+  float2* obuf = lbase + NL * G::LP;     // H x W: the crop rows (then the refined ones)
+  float2* pbuf = obuf + H * W;           // M x H x W: the probe rows
+  uint16_t* cbuf = reinterpret_cast<uint16_t*>(pbuf + M * H * W);  // W x H counts [u][cl]
   __shared__ float red_o[32], red_e[32];
   __shared__ float xch[2];               // read by the cluster: [0] crop maximum, [1] error
   __shared__ float s_pmax;
 
-  const int M = q.M, NL = q.NL;
-  const int CS = M * S;
-  const int rank = (int)cluster_rank();
-  const int k = rank / S, s = rank - k * S;
-  const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+  const int s = (int)cluster_rank();
+  const int cid = blockIdx.x / S, ncl = gridDim.x / S;
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
   const bool act = line < NL;
   float2* lbuf = lbase + (act ? line : 0) * G::LP;
-  const int r0 = s * HS;  // first row of the slab; also the first column of its column lines
+  const int r0 = s * H;  // first row of the row slab, first column of the column slab
   const int nw = blockDim.x >> 5;
-  const int nown = (HS - k + M - 1) / M;  // slab rows lr = k, k + M, ... this CTA owns
-  float2* Am[S];                          // mode k's slabs
-#pragma unroll
-  for (int t = 0; t < S; ++t) Am[t] = cluster_map(A, (unsigned)(k * S + t));
+  const int nfar = M * W * H;  // far-field values of one slab (either kind)
 
   pdl_trigger();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = q.tw[e];
@@ -91,25 +93,44 @@ __global__ void __launch_bounds__(kPatchMaxThreads, 1) k_patch(const __grid_cons
   for (int lp = cid; lp < q.npatch; lp += ncl) {
     const int j = q.ids[lp];
     const int2 cc = q.corners[j];
-    if (!first) cluster_sync();  // the previous patch's remote reads of the slabs are over
+    {
+      // requested now, used after the forward DFTs: every mode's probe rows of
+      // the row slab (for the update) and the counts of the column slab
+      // (stored fftshifted: row (u + W/2) mod W, columns (c + W/2) mod W;
+      // 16-byte pieces that never wrap)
+      for (int i = threadIdx.x; i < M * H * (W / 2); i += blockDim.x) {
+        const int row = i / (W / 2), h = i - row * (W / 2);  // row = k * H + r
+        const int k = row / H, r = row - k * H;
+        cp_async<16>(pbuf + row * W + 2 * h, q.P + ((size_t)k * W + r0 + r) * W + 2 * h);
+      }
+      const uint16_t* Ij = q.I + (size_t)j * W * W;
+      constexpr int ppr = H / 8;
+      for (int i = threadIdx.x; i < W * ppr; i += blockDim.x) {
+        const int u = i / ppr, h = i - u * ppr;
+        const int su = (u + W / 2) % W, sc = (r0 + 8 * h + W / 2) % W;
+        cp_async<16>(cbuf + u * H + 8 * h, Ij + (size_t)su * W + sc);
+      }
+      cp_async_commit();
+    }
 
-    // ---- forward row DFTs of psi_k = P_k o_j; with XCORR_A also this CTA's
-    // rows of the crop itself (registration plane M)
-    const int nlines = HS + (q.refine == 1 ? nown : 0);
+    // ---- forward row DFTs of psi_k = P_k o_j on the row slab; with XCORR_A
+    // also the crop rows themselves (registration plane M)
+    const int nrl = M * H + (q.refine == 1 ? H : 0);
     float omax = 0.f;
-    for (int t0 = 0; t0 < nlines; t0 += NL) {
+    for (int t0 = 0; t0 < nrl; t0 += NL) {
       const int t = t0 + line;
-      const bool on = act && t < nlines;
-      const bool crop = t >= HS;
-      const int lr = crop ? k + M * (t - HS) : t;
+      const bool on = act && t < nrl;
+      const bool crop = t >= M * H;
+      const int k = crop ? M : t / H, r = t - k * H;
       if (on && lane < G::N2) {
-        const float2* orow = q.O + (size_t)(cc.x + r0 + lr) * q.Hx + cc.y;
-        const float2* prow = q.P + ((size_t)k * W + r0 + lr) * W;
+        const float2* orow = q.O + (size_t)(cc.x + r0 + r) * q.Hx + cc.y;
+        const float2* prow = q.P + ((size_t)(crop ? 0 : k) * W + r0 + r) * W;
         float2 v[G::N1];
 #pragma unroll
         for (int n1 = 0; n1 < G::N1; ++n1) {
           const int c = G::N2 * n1 + lane;
           const float2 o = orow[c];
+          if (k == 0) obuf[r * W + c] = o;
           v[n1] = crop ? o : cmul(__ldg(prow + c), o);
           omax = fmaxf(omax, cabs2(o));
         }
@@ -119,8 +140,8 @@ __global__ void __launch_bounds__(kPatchMaxThreads, 1) k_patch(const __grid_cons
       if (on && lane < G::N1) {
         float2 z[G::N2];
         fwd_step3<W>(z, lane, lbuf);
-        float2* dst = crop ? q.scratch + (((size_t)lp * q.npl + M) * W + r0 + lr) * W
-                           : A + lr * PITCH;
+        float2* dst = crop ? q.scratch + (((size_t)lp * q.npl + M) * W + r0 + r) * W
+                           : RA + (k * H + r) * PITCH;
 #pragma unroll
         for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
       }
@@ -134,23 +155,44 @@ __global__ void __launch_bounds__(kPatchMaxThreads, 1) k_patch(const __grid_cons
       for (int i = 0; i < nw; ++i) m = fmaxf(m, red_o[i]);
       xch[0] = m;
     }
-    cluster_sync();  // rows transformed; each slab's crop maximum posted
+    cluster_sync();  // B1: every row slab transformed; every slab's crop maximum posted
     float om = 0.f;  // max_r |o_j(r)|^2 over the whole crop (exact: a maximum)
 #pragma unroll
-    for (int t = 0; t < S; ++t) om = fmaxf(om, *cluster_map(&xch[0], (unsigned)(k * S + t)));
+    for (int t = 0; t < S; ++t) om = fmaxf(om, *cluster_map(&xch[0], (unsigned)t));
 
-    // ---- forward column DFTs of mode k, columns [r0, r0 + HS), in place
-    for (int t0 = 0; t0 < HS; t0 += NL) {
+    // ---- gather the column slab: CA[k][cl][u] = RA of CTA u / H, [k][u mod H][r0 + cl]
+    // (consecutive threads read consecutive columns of one row; four loads in flight)
+    for (int e0 = threadIdx.x; e0 < nfar; e0 += 4 * blockDim.x) {
+      float2 v[4];
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const int e = e0 + q4 * blockDim.x;
+        if (e < nfar) {
+          const int k = e / (W * H), rem = e - k * (W * H), u = rem / H, cl = rem - u * H;
+          const int ow = u / H;
+          v[q4] = cluster_map(RA, (unsigned)ow)[(k * H + u - ow * H) * PITCH + r0 + cl];
+        }
+      }
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const int e = e0 + q4 * blockDim.x;
+        if (e < nfar) {
+          const int k = e / (W * H), rem = e - k * (W * H), u = rem / H, cl = rem - u * H;
+          CA[(k * H + cl) * PITCH + u] = v[q4];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- forward column DFTs (local, in place)
+    for (int t0 = 0; t0 < M * H; t0 += NL) {
       const int t = t0 + line;
-      const bool on = act && t < HS;
-      const int c = r0 + t;
+      const bool on = act && t < M * H;
+      float2* col = CA + t * PITCH;  // column line t = k * H + cl
       if (on && lane < G::N2) {
         float2 v[G::N1];
 #pragma unroll
-        for (int n1 = 0; n1 < G::N1; ++n1) {
-          const int ow = (G::N2 * n1) / HS;  // a constant once unrolled
-          v[n1] = Am[ow][(G::N2 * n1 - ow * HS + lane) * PITCH + c];
-        }
+        for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = col[G::N2 * n1 + lane];
         fwd_step1<W>(v, lane, tw, lbuf);
       }
       line_sync<W>();
@@ -158,46 +200,36 @@ __global__ void __launch_bounds__(kPatchMaxThreads, 1) k_patch(const __grid_cons
         float2 z[G::N2];
         fwd_step3<W>(z, lane, lbuf);
 #pragma unroll
-        for (int k2 = 0; k2 < G::N2; ++k2) {
-          const int ow = (G::N1 * k2) / HS;
-          Am[ow][(G::N1 * k2 - ow * HS + lane) * PITCH + c] = z[k2];
-        }
+        for (int k2 = 0; k2 < G::N2; ++k2) col[lane + G::N1 * k2] = z[k2];
       }
       line_sync<W>();
     }
-    cluster_sync();  // Psi_k complete in every slab
+    cp_async_wait<0>();  // this thread's probe and count pieces (the barrier shows all)
+    __syncthreads();
 
-    // ---- modulus constraint on this CTA's rows of slab s, every mode (the
-    // three-pass column kernel's arithmetic, in the same order)
+    // ---- modulus constraint on the column slab (the three-pass column
+    // kernel's arithmetic, in the same order over the modes)
     float e_acc = 0.f;
     {
       const float f2 = q.inv_w * q.inv_w;
-      const uint16_t* Ij = q.I + (size_t)j * W * W;
-      for (int e = threadIdx.x; e < nown * W; e += blockDim.x) {
-        const int rw = e / W, c = e - rw * W;
-        const int lr = k + M * rw, u = r0 + lr, off = lr * PITCH + c;
-        const float cnt = (float)__ldg(Ij + (size_t)((u + W / 2) % W) * W + (c + W / 2) % W);
-        float2 z[8];
+      for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+        const int u = e / H, cl = e - u * H;
+        const float cnt = (float)cbuf[e];
         float sum = 0.f;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < M) {
-            z[jj] = cluster_map(A, (unsigned)(jj * S + s))[off];
-            sum += cabs2(z[jj]);
-          }
-        }
+        for (int k = 0; k < M; ++k) sum += cabs2(CA[(k * H + cl) * PITCH + u]);
         const float sI = sqrt_rs(cnt);
         const float a = __fmul_rn(sqrt_rs(sum), q.inv_w);
         const float d = __fsub_rn(a, sI);
         e_acc = fmaf(d, d, e_acc);
         const float f = __fmul_rn(__fdividef(sI, __fadd_rn(a, q.a.eps)), f2);
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          if (jj < M) cluster_map(A, (unsigned)(jj * S + s))[off] = cscale(z[jj], f);
+        for (int k = 0; k < M; ++k) {
+          float2* z = CA + (k * H + cl) * PITCH + u;
+          *z = cscale(*z, f);
+        }
         if (q.refine == 2) {
           // XCORR_B: model intensity and counts, unshifted, as real parts of
           // registration planes M and M + 1
-          float2* pl = q.scratch + ((size_t)lp * q.npl + M) * W * W + (size_t)u * W + c;
+          float2* pl = q.scratch + ((size_t)lp * q.npl + M) * W * W + (size_t)u * W + r0 + cl;
           pl[0] = make_float2(sum * f2, 0.f);
           pl[(size_t)W * W] = make_float2(cnt, 0.f);
         }
@@ -211,52 +243,69 @@ __global__ void __launch_bounds__(kPatchMaxThreads, 1) k_patch(const __grid_cons
       for (int i = 0; i < nw; ++i) t += red_e[i];  // fixed order
       xch[1] = t;
     }
-    cluster_sync();  // every mode scaled; every CTA's error partial posted
-    if (rank == 0 && threadIdx.x == 0) {
+
+    // ---- inverse column DFTs (local, in place)
+    for (int t0 = 0; t0 < M * H; t0 += NL) {
+      const int t = t0 + line;
+      const bool on = act && t < M * H;
+      float2* col = CA + t * PITCH;
+      if (on && lane < G::N1) {
+        float2 z[G::N2];
+#pragma unroll
+        for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = col[lane + G::N1 * k2];
+        inv_stepA<W>(z, lane, tw, lbuf);
+      }
+      line_sync<W>();
+      if (on && lane < G::N2) {
+        float2 v[G::N1];
+        inv_stepB<W>(v, lane, lbuf);
+#pragma unroll
+        for (int n1 = 0; n1 < G::N1; ++n1) col[G::N2 * n1 + lane] = v[n1];
+      }
+      line_sync<W>();
+    }
+    cluster_sync();  // B2: every gather is over; every error partial posted
+    if (s == 0 && threadIdx.x == 0) {
       float t = 0.f;
-      for (int r = 0; r < CS; ++r) t += *cluster_map(&xch[1], (unsigned)r);  // rank order
+      for (int r = 0; r < S; ++r) t += *cluster_map(&xch[1], (unsigned)r);  // rank order
       float* ep = q.err_part + (size_t)j * q.nb;
       ep[0] = t;
       for (int i = 1; i < q.nb; ++i) ep[i] = 0.f;
     }
 
-    // ---- inverse column DFTs, in place
-    for (int t0 = 0; t0 < HS; t0 += NL) {
-      const int t = t0 + line;
-      const bool on = act && t < HS;
-      const int c = r0 + t;
-      if (on && lane < G::N1) {
-        float2 z[G::N2];
+    // ---- scatter the column slab back into the row slabs
+    for (int e0 = threadIdx.x; e0 < nfar; e0 += 4 * blockDim.x) {
+      float2 v[4];
 #pragma unroll
-        for (int k2 = 0; k2 < G::N2; ++k2) {
-          const int ow = (G::N1 * k2) / HS;
-          z[k2] = Am[ow][(G::N1 * k2 - ow * HS + lane) * PITCH + c];
-        }
-        inv_stepA<W>(z, lane, tw, lbuf);
-      }
-      line_sync<W>();
-      if (on && lane < G::N2) {
-        float2 v[G::N1];
-        inv_stepB<W>(v, lane, lbuf);
-#pragma unroll
-        for (int n1 = 0; n1 < G::N1; ++n1) {
-          const int ow = (G::N2 * n1) / HS;
-          Am[ow][(G::N2 * n1 - ow * HS + lane) * PITCH + c] = v[n1];
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const int e = e0 + q4 * blockDim.x;
+        if (e < nfar) {
+          const int k = e / (W * H), rem = e - k * (W * H), u = rem / H, cl = rem - u * H;
+          v[q4] = CA[(k * H + cl) * PITCH + u];
         }
       }
-      line_sync<W>();
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const int e = e0 + q4 * blockDim.x;
+        if (e < nfar) {
+          const int k = e / (W * H), rem = e - k * (W * H), u = rem / H, cl = rem - u * H;
+          const int ow = u / H;
+          cluster_map(RA, (unsigned)ow)[(k * H + u - ow * H) * PITCH + r0 + cl] = v[q4];
+        }
+      }
     }
-    cluster_sync();
+    cluster_sync();  // B3: every row slab holds its inverse-column-transformed rows
 
-    // ---- inverse row DFTs of the slab: psi'_k (unnormalised by W^2, which
-    // the constraint factor carries)
-    for (int t0 = 0; t0 < HS; t0 += NL) {
+    // ---- inverse row DFTs: psi'_k (unnormalised by W^2, which the constraint
+    // factor carries)
+    for (int t0 = 0; t0 < M * H; t0 += NL) {
       const int t = t0 + line;
-      const bool on = act && t < HS;
+      const bool on = act && t < M * H;
+      float2* row = RA + t * PITCH;  // row line t = k * H + r
       if (on && lane < G::N1) {
         float2 z[G::N2];
 #pragma unroll
-        for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = A[t * PITCH + lane + G::N1 * k2];
+        for (int k2 = 0; k2 < G::N2; ++k2) z[k2] = row[lane + G::N1 * k2];
         inv_stepA<W>(z, lane, tw, lbuf);
       }
       line_sync<W>();
@@ -264,89 +313,75 @@ __global__ void __launch_bounds__(kPatchMaxThreads, 1) k_patch(const __grid_cons
         float2 v[G::N1];
         inv_stepB<W>(v, lane, lbuf);
 #pragma unroll
-        for (int n1 = 0; n1 < G::N1; ++n1) A[t * PITCH + G::N2 * n1 + lane] = v[n1];
+        for (int n1 = 0; n1 < G::N1; ++n1) row[G::N2 * n1 + lane] = v[n1];
       }
       line_sync<W>();
     }
-    cluster_sync();  // psi'_k complete in every slab
+    __syncthreads();
 
     // ---- object update (written in place: the group's boxes are disjoint)
-    // and the probe sums of this cluster's slot, on this CTA's rows
+    // and the probe sums of this cluster's slot, on the row slab
     {
       const bool acc = !first || q.accumulate;
       const float omb = 1.f - q.a.beta, omg = 1.f - q.a.gamma, bom = q.a.beta * om;
       const int slot = cid;
-      for (int e = threadIdx.x; e < nown * W; e += blockDim.x) {
-        const int rw = e / W, c = e - rw * W;
-        const int lr = k + M * rw, r = r0 + lr, off = lr * PITCH + c;
-        float2* op = q.O + (size_t)(cc.x + r) * q.Hx + cc.y + c;
-        float* pd = q.pden + ((size_t)slot * W + r) * W + c;
-        const float2 o = *op;
+      for (int e = threadIdx.x; e < H * W; e += blockDim.x) {
+        const int r = e / W, c = e - r * W, gr = r0 + r;
+        const float2 o = obuf[e];
+        float* pd = q.pden + ((size_t)slot * W + gr) * W + c;
         const float pd0 = acc ? *pd : 0.f;
-        float2 pv[8], vv[8], nv[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < M) {
-            pv[jj] = __ldg(q.P + ((size_t)jj * W + r) * W + c);
-            vv[jj] = cluster_map(A, (unsigned)(jj * S + s))[off];
-            nv[jj] = acc ? q.pnum[(((size_t)slot * M + jj) * W + r) * W + c] : make_float2(0.f, 0.f);
-          }
-        }
         float2 sT = make_float2(0.f, 0.f);
         float pint = 0.f;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < M) {
-            const float2 D = csub(vv[jj], cmul(pv[jj], o));
-            sT = cadd(sT, cmulc(D, pv[jj]));
-            pint += cabs2(pv[jj]);
-            const float2 nm = cmulc(D, o);
-            nv[jj] = acc ? cadd(nv[jj], nm) : nm;
-          }
+        for (int k = 0; k < M; ++k) {
+          const float2 p = pbuf[(k * H + r) * W + c];
+          const float2 v = RA[(k * H + r) * PITCH + c];
+          float2* pn = q.pnum + (((size_t)slot * M + k) * W + gr) * W + c;
+          const float2 D = csub(v, cmul(p, o));
+          sT = cadd(sT, cmulc(D, p));
+          pint += cabs2(p);
+          const float2 nm = cmulc(D, o);
+          *pn = acc ? cadd(*pn, nm) : nm;
         }
         const float dn = fmaf(omg, pint, gden);
         const float sc = dn > 0.f ? q.a.alpha_O / dn : 0.f;  // a zero denominator has a zero numerator
         const float2 onw = make_float2(fmaf(sc, sT.x, o.x), fmaf(sc, sT.y, o.y));
-        *op = onw;
-        if (q.refine == 1) A[off] = onw;  // only this CTA reads its own rows
+        q.O[(size_t)(cc.x + gr) * q.Hx + cc.y + c] = onw;
+        if (q.refine == 1) obuf[e] = onw;
         const float dv = fmaf(omb, cabs2(o), bom);
         *pd = acc ? pd0 + dv : dv;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          if (jj < M) q.pnum[(((size_t)slot * M + jj) * W + r) * W + c] = nv[jj];
       }
       osum_local += om;
     }
 
-    // ---- XCORR_A: forward row DFTs of this CTA's rows of the refined crop
-    // (registration plane M + 1)
+    // ---- XCORR_A: forward row DFTs of the refined crop rows (registration
+    // plane M + 1)
     if (q.refine == 1) {
       __syncthreads();
-      for (int t0 = 0; t0 < nown; t0 += NL) {
+      for (int t0 = 0; t0 < H; t0 += NL) {
         const int t = t0 + line;
-        const bool on = act && t < nown;
-        const int lr = k + M * t;
+        const bool on = act && t < H;
         if (on && lane < G::N2) {
           float2 v[G::N1];
 #pragma unroll
-          for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = A[lr * PITCH + G::N2 * n1 + lane];
+          for (int n1 = 0; n1 < G::N1; ++n1) v[n1] = obuf[t * W + G::N2 * n1 + lane];
           fwd_step1<W>(v, lane, tw, lbuf);
         }
         line_sync<W>();
         if (on && lane < G::N1) {
           float2 z[G::N2];
           fwd_step3<W>(z, lane, lbuf);
-          float2* dst = q.scratch + (((size_t)lp * q.npl + M + 1) * W + r0 + lr) * W;
+          float2* dst = q.scratch + (((size_t)lp * q.npl + M + 1) * W + r0 + t) * W;
 #pragma unroll
           for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = z[k2];
         }
         line_sync<W>();
       }
     }
+    __syncthreads();  // obuf, lbuf and cbuf are refilled by the next patch
     first = false;
   }
-  cluster_sync();  // no CTA leaves while another may still read its slab
-  if (rank == 0 && threadIdx.x == 0 && !first)
+  cluster_sync();  // no CTA leaves while another may still touch its shared memory
+  if (s == 0 && threadIdx.x == 0 && !first)
     q.osum[cid] = q.accumulate ? q.osum[cid] + osum_local : osum_local;
 }
 
@@ -399,7 +434,7 @@ PatchGeo make_patch_geo(int W, int M, int S) {
   g.M = M;
   g.S = S;
   void* f = patch_kernel(W, S);
-  if (!f || M < 1 || M * S > 8) return g;
+  if (!f || M < 1 || S > 8) return g;
   int L = 16, LP = 0;
   switch (W) {
     case 32: patch_line<32>(L, LP); break;
@@ -407,24 +442,24 @@ PatchGeo make_patch_geo(int W, int M, int S) {
     case 96: patch_line<96>(L, LP); break;
     default: patch_line<128>(L, LP); break;
   }
-  const int HS = W / S;
-  if (HS < M) return g;  // every CTA of a slab owns at least one row
-  g.NL = std::min(HS, 32);
-  g.NT = (g.NL * L + 31) / 32 * 32;
-  if (g.NT > kPatchMaxThreads) return g;
-  g.sm = (size_t)(W + HS * (W + 1) + g.NL * LP) * sizeof(float2);
+  const int H = W / S;
+  // lines per round: as many as the launch bound holds, at most one round
+  g.NL = std::min(kPatchMaxThreads / L, M * H);
+  g.NT = kPatchMaxThreads;  // the element-wise phases use every thread
+  g.sm = (size_t)(W + 2 * M * H * (W + 1) + g.NL * LP + H * W + M * H * W) * sizeof(float2) +
+         (size_t)W * H * sizeof(uint16_t);
   if (g.sm > (size_t)smem_optin() - 512) return g;
   if (allow_max_smem(f) != cudaSuccess) {
     cudaGetLastError();
     return g;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(M * S);
+  cfg.gridDim = dim3(S);
   cfg.blockDim = dim3(g.NT);
   cfg.dynamicSmemBytes = g.sm;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = M * S;
+  at[0].val.clusterDim.x = S;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -443,13 +478,13 @@ cudaError_t launch_patch(const PatchGeo& g, const PatchArgs& a, int nclusters, c
   if (!f || g.ncap < 1 || nclusters < 1 || nclusters > g.ncap || a.M != g.M)
     return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nclusters * g.M * g.S);
+  cfg.gridDim = dim3(nclusters * g.S);
   cfg.blockDim = dim3(g.NT);
   cfg.dynamicSmemBytes = g.sm;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = g.M * g.S;
+  at[0].val.clusterDim.x = g.S;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;

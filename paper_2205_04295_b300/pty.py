@@ -464,7 +464,7 @@ class Problem:
 
     def set_tiling(self, R=0, ppc=0, CB=0, scratch_bytes=0, ppcb=0, fused=0):
         """fused = S > 0: the single-kernel patch path (W <= 128), a cluster
-        of M x S CTAs per patch; 0: the three passes."""
+        of S CTAs per patch; 0: the three passes."""
         check(lib().pty_set_tiling(self.h, ctypes.byref(Tiling(R, ppc, CB, scratch_bytes, ppcb,
                                                                fused))))
 

@@ -1,5 +1,6 @@
 """The fused single-kernel patch path for W <= 128 (one thread-block cluster
-of M x S CTAs per patch, the W x W planes in shared memory, no far-field
+of S CTAs per patch, each holding every mode's W/S rows and, between two
+transposes through distributed shared memory, W/S columns; no far-field
 scratch) against the FP64 oracle on the same seeded inputs and the same
 grouped schedule, and against the three-pass path.
 
@@ -65,10 +66,10 @@ def check_one_iteration(wl, d, S, scratch_bytes=0, **kw):
 CASES = {
     "w32_m2": (lambda: synth.tiny(W=32, M=2, ny=5, nx=5, step=6.0), (1, 2, 4)),
     "w64_m1_plain": (lambda: synth.plain_rpie_64(), (1, 2, 4, 8)),
-    "w64_m4": (lambda: synth.tiny(W=64, M=4, ny=4, nx=4, step=10.0, seed=21), (1, 2)),
-    "w96_m2": (lambda: synth.tiny(W=96, M=2, ny=3, nx=4, step=20.0, seed=3), (1, 2, 4)),
-    "w128_m3": (lambda: synth.tiny(W=128, M=3, ny=3, nx=3, step=24.0, seed=4, photons=1e6),
-                (1, 2)),
+    "w64_m4": (lambda: synth.tiny(W=64, M=4, ny=4, nx=4, step=10.0, seed=21), (4, 8)),
+    "w96_m1": (lambda: synth.tiny(W=96, M=1, ny=3, nx=4, step=20.0, seed=26), (2, 4)),
+    "w96_m2": (lambda: synth.tiny(W=96, M=2, ny=3, nx=4, step=20.0, seed=3), (4,)),
+    "w128_m3": (lambda: synth.tiny(W=128, M=3, ny=3, nx=3, step=24.0, seed=4, photons=1e6), (8,)),
     "w128_m1": (lambda: synth.tiny(W=128, M=1, ny=3, nx=3, step=24.0, seed=22), (4, 8)),
 }
 PARAMS = [(c, S) for c, (_, Ss) in CASES.items() for S in Ss]
@@ -95,7 +96,7 @@ def test_single_group_matches_three_pass():
     d = build(wl)
     from paper_2205_04295_b300 import pty
     outs = []
-    for S in (0, 1, 2):
+    for S in (0, 2, 4):
         prob = problem(wl, d, S)
         assert len(prob.groups()) == 1
         e = prob.run(1, pty.rpie_params())[0]
@@ -203,7 +204,11 @@ def test_unsupported_fused_tilings_are_rejected():
         with pytest.raises(pty.PtyError, match="EINVAL"):
             prob.set_tiling(fused=S)
     with pytest.raises(pty.PtyError, match="does not fit"):
-        prob.set_tiling(fused=4)  # 3 modes x 4 slabs > 8 CTAs per cluster
+        prob.set_tiling(fused=1)  # two 3-mode 64 x 64 slabs exceed the shared memory
+    assert prob.tiling()["fused"] == 0
+    prob.set_tiling(fused=4)
+    assert prob.tiling()["fused"] == 4
+    prob.set_tiling()
     assert prob.tiling()["fused"] == 0
     wl2 = synth.tiny(W=256, M=1, ny=2, nx=2, step=40.0)
     prob2 = problem(wl2, build(wl2))
