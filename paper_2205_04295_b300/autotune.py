@@ -4,6 +4,8 @@ For a (W, M) class it searches, in stages, the tiling of one problem:
   1. CB, columns per CTA of the column pass;
   2. R x ppc, rows and patches per CTA of the two row passes;
   3. the far-field scratch budget (the chunk of a group held in L2);
+  4. for W <= 128, the fused single-kernel patch path with S = 1, 2, 4, 8
+     CTAs per patch, kept where it beats the three passes;
 timing one full iteration per candidate with CUDA events on the library's
 stream (results never depend on the tiling beyond the summation order of the
 probe sums).  For the batched form it searches the task granularity (how many
@@ -68,7 +70,8 @@ def tune_problem(prob, params=None, reps=2):
     def trial(**t):
         cfg = dict(best)
         cfg.update(t)
-        prob.set_tiling(cfg["R"], cfg["ppc"], cfg["CB"], cfg["scratch_bytes"], cfg["ppcb"])
+        prob.set_tiling(cfg["R"], cfg["ppc"], cfg["CB"], cfg["scratch_bytes"], cfg["ppcb"],
+                        cfg.get("fused", 0))
         ms = time_iteration(prob, params, reps)
         trials.append(dict(cfg, ms=ms))
         return ms, cfg
@@ -82,7 +85,50 @@ def tune_problem(prob, params=None, reps=2):
         ms, cfg = min(results, key=lambda x: x[0])
         best = cfg
         best_ms = ms
-    prob.set_tiling(best["R"], best["ppc"], best["CB"], best["scratch_bytes"], best["ppcb"])
+    best, best_ms = _fused_stage(prob, best, best_ms, trial)
+    _set(prob, best)
+    return {"tiling": best, "ms": best_ms, "trials": trials}
+
+
+def _set(prob, t):
+    prob.set_tiling(t["R"], t["ppc"], t["CB"], t["scratch_bytes"], t.get("ppcb", 0),
+                    t.get("fused", 0))
+
+
+def _fused_stage(prob, best, best_ms, trial):
+    """Stage 4: the fused patch kernel (W <= 128) on top of the best
+    three-pass tiling (whose scratch budget it keeps for registration
+    chunks); slab counts the shared memory does not hold are skipped."""
+    if prob.W > 128:
+        return best, best_ms
+    for S in (1, 2, 4, 8):
+        try:
+            ms, cfg = trial(fused=S)
+        except pty.PtyError:
+            continue
+        if ms < best_ms:
+            best, best_ms = cfg, ms
+    return best, best_ms
+
+
+def tune_fused(prob, params=None, reps=2):
+    """Stage 4 alone, starting from the problem's current (three-pass) tiling."""
+    params = params or pty.rpie_params()
+    trials = []
+    base = dict(prob.tiling())
+    base["fused"] = 0
+
+    def trial(**t):
+        cfg = dict(base)
+        cfg.update(t)
+        _set(prob, cfg)
+        ms = time_iteration(prob, params, reps)
+        trials.append(dict(cfg, ms=ms))
+        return ms, cfg
+
+    ms0, _ = trial()
+    best, best_ms = _fused_stage(prob, base, ms0, trial)
+    _set(prob, best)
     return {"tiling": best, "ms": best_ms, "trials": trials}
 
 
@@ -156,13 +202,17 @@ def apply(prob, table=None):
     ent = table.get("%dx%d" % (prob.W, prob.M))
     if ent:
         t = ent["tiling"]
-        prob.set_tiling(t["R"], t["ppc"], t["CB"], t["scratch_bytes"], t.get("ppcb", 0))
+        _set(prob, t)
         return t
     return None
 
 
 def _workload(W, M):
     from . import synth
+    if (W, M) == (64, 1):
+        return synth.plain_rpie_64()  # the 10 x 10 raster of the plain workload
+    if (W, M) == (128, 3):
+        return synth.refine_128()  # the 40 x 40 jittered raster of the refinement workload
     if W == 256 and M == 4:
         return synth.sweep_256()  # the 40 000-position raster: its group sizes
     if W == 256:
@@ -179,6 +229,8 @@ def main():
     ap.add_argument("--classes", default="256x5,256x4,64x1,64x2,64x3,96x1,96x2,96x3,128x1,"
                                         "128x2,128x3,192x1,192x2,192x3")
     ap.add_argument("--out", default=CACHE)
+    ap.add_argument("--fused-only", action="store_true",
+                    help="only stage 4 (the fused patch kernel) on top of each cached tiling")
     ap.add_argument("--batch", action="store_true",
                     help="also tune the 64-problem batched workload (task splits, group cap)")
     args = ap.parse_args()
@@ -190,7 +242,12 @@ def main():
         prob = pty.Problem(wl.W, wl.M, wl.N, wl.Hy, wl.Hx)
         prob.set_data(synth.counts_u16(d["I"]), torch.from_numpy(d["pos"]).cuda(),
                       torch.from_numpy(d["O0"]).cuda(), torch.from_numpy(d["P0"]).cuda())
-        res = tune_problem(prob)
+        if args.fused_only and cls in table:
+            apply(prob, table)
+            res = tune_fused(prob)
+            res["trials"] = table[cls].get("trials", []) + res["trials"]
+        else:
+            res = tune_problem(prob)
         res["workload"] = wl.name
         table[cls] = res
         print(cls, res["tiling"], "%.3f ms" % res["ms"], flush=True)
