@@ -111,11 +111,12 @@ def _fused_stage(prob, best, best_ms, trial):
     return best, best_ms
 
 
-def tune_fused(prob, params=None, reps=2):
-    """Stage 4 alone, starting from the problem's current (three-pass) tiling."""
+def tune_fused(prob, params=None, reps=2, base=None):
+    """Stage 4 alone, starting from `base` (a three-pass tiling; default the
+    problem's current one)."""
     params = params or pty.rpie_params()
     trials = []
-    base = dict(prob.tiling())
+    base = dict(base or prob.tiling())
     base["fused"] = 0
 
     def trial(**t):
@@ -243,8 +244,7 @@ def main():
         prob.set_data(synth.counts_u16(d["I"]), torch.from_numpy(d["pos"]).cuda(),
                       torch.from_numpy(d["O0"]).cuda(), torch.from_numpy(d["P0"]).cuda())
         if args.fused_only and cls in table:
-            apply(prob, table)
-            res = tune_fused(prob)
+            res = tune_fused(prob, base=table[cls]["tiling"])
             res["trials"] = table[cls].get("trials", []) + res["trials"]
         else:
             res = tune_problem(prob)
