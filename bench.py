@@ -51,13 +51,16 @@ def algorithmic(W, M):
 
 
 def per_pass_flops(W, M):
-    """Algorithmic flops per pattern update of each pass."""
+    """Algorithmic flops per pattern update of each pass (and of the fused
+    patch kernel, which does all three)."""
     import math
     lw = math.log2(W)
     row = 5.0 * W * W * lw          # W row DFTs of length W
-    return {"rows_fwd": M * row + 6 * M * W * W,
-            "cols": 2 * M * row + (4 * M + 10) * W * W,
-            "rows_inv": M * row + (24 * M + 10) * W * W}
+    f = {"rows_fwd": M * row + 6 * M * W * W,
+         "cols": 2 * M * row + (4 * M + 10) * W * W,
+         "rows_inv": M * row + (24 * M + 10) * W * W}
+    f["patch"] = f["rows_fwd"] + f["cols"] + f["rows_inv"]
+    return f
 
 
 # DRAM bytes per pattern update of each pass, warm L2: ncu
@@ -388,7 +391,8 @@ def run_ours(args, wl, rank, world, local):
     kst = prob.stats(reset=True)
     prob.profile(0)
     pf = per_pass_flops(wl.W, wl.M)
-    kinds = [k for k in ("rows_fwd", "cols", "rows_inv", "probe", "reduce") if kst["launches"][k]]
+    kinds = [k for k in ("rows_fwd", "cols", "rows_inv", "patch", "probe", "reduce")
+             if kst["launches"][k]]
     total_ms = sum(kst["ms"][k] for k in kinds)
     dom = max(kinds, key=lambda k: kst["ms"][k])
     n_dom = kst["launches"][dom]
