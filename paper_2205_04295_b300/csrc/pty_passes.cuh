@@ -357,42 +357,62 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
     float e = 0.f;
     {
       const float f2 = inv_w * inv_w;
-      for (int el = threadIdx.x; el < CB * W; el += blockDim.x) {
-        const int u = el / CB, cl = el - u * CB;
-        float s = 0.f;
+      // two detector pixels per step: their mode sums are loaded before
+      // either factor is stored (the store may alias the next loads)
+      const int n = CB * W, st = blockDim.x;
+      for (int el0 = threadIdx.x; el0 < n; el0 += 2 * st) {
+        const bool two = el0 + st < n;
+        float s2[2] = {0.f, 0.f};
+        float c2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int el = el0 + h * st;
+          if (h == 0 || two) {
+            const int u = el / CB, cl = el - u * CB;
 #pragma unroll 4
-        for (int kk = 0; kk < M; ++kk) s += Sb[(kk * W + u) * CB + cl];
-        const float sI = sqrt_rs((float)cn[el]);
-        if (!GRAD) {
-          // rounded products and sums written out (no contraction), as in
-          // the fused patch kernel
-          const float a = __fmul_rn(sqrt_rs(s), inv_w);
-          const float d = __fsub_rn(a, sI);
-          e = fmaf(d, d, e);
-          // quotient by a reciprocal-multiply (within 2 ulp of the division)
-          Sb[u * CB + cl] = __fmul_rn(__fdividef(sI, __fadd_rn(a, eps)), f2);
-          if (xb >= 0) {
-            // XCORR_B: the model intensity and the counts, unshifted, as the
-            // real parts of scratch planes xb and xb + 1
-            float2* pl = scratch + ((size_t)lp * npl + xb) * W * W + (size_t)u * W + c0 + cl;
-            pl[0] = make_float2(s * f2, 0.f);
-            pl[(size_t)W * W] = make_float2((float)cn[el], 0.f);
+            for (int kk = 0; kk < M; ++kk) s2[h] += Sb[(kk * W + u) * CB + cl];
+            c2[h] = (float)cn[el];
           }
-        } else {
-          const float a = sqrt_rs(fmaf(s, f2, eps));
-          const float d = a - sI;
-          e = fmaf(d, d, e);
-          Sb[u * CB + cl] = 2.f * (1.f - __fdividef(sI, a)) * f2;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          const int el = el0 + h * st;
+          const int u = el / CB, cl = el - u * CB;
+          const float s = s2[h];
+          const float sI = sqrt_rs(c2[h]);
+          if (!GRAD) {
+            // rounded products and sums written out (no contraction), as in
+            // the fused patch kernel
+            const float a = __fmul_rn(sqrt_rs(s), inv_w);
+            const float d = __fsub_rn(a, sI);
+            e = fmaf(d, d, e);
+            // quotient by a reciprocal-multiply (within 2 ulp of the division)
+            Sb[u * CB + cl] = __fmul_rn(__fdividef(sI, __fadd_rn(a, eps)), f2);
+            if (xb >= 0) {
+              // XCORR_B: the model intensity and the counts, unshifted, as the
+              // real parts of scratch planes xb and xb + 1
+              float2* pl = scratch + ((size_t)lp * npl + xb) * W * W + (size_t)u * W + c0 + cl;
+              pl[0] = make_float2(s * f2, 0.f);
+              pl[(size_t)W * W] = make_float2(c2[h], 0.f);
+            }
+          } else {
+            const float a = sqrt_rs(fmaf(s, f2, eps));
+            const float d = a - sI;
+            e = fmaf(d, d, e);
+            Sb[u * CB + cl] = 2.f * (1.f - __fdividef(sI, a)) * f2;
+          }
         }
       }
     }
     e = warp_sum(e);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      float t = 0.f;
-      for (int i = 0; i < nw; ++i) t += red[i];  // fixed order
-      err_part[(size_t)j * (W / CB) + bx] = t;
+    if (threadIdx.x >= blockDim.x - 32) {
+      // the last warp sums the warp partials (a fixed shuffle tree)
+      const int l = threadIdx.x & 31;
+      const float t = warp_sum(l < nw ? red[l] : 0.f);
+      if (l == 0) err_part[(size_t)j * (W / CB) + bx] = t;
     }
     if (act && lane < G::N1) {
 #pragma unroll
@@ -447,6 +467,64 @@ PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 c
     }
   }
   stage_crop_rows<W>(O, Hx, cc, R, r0, ost);
+}
+
+// A lane's object-update terms for its N1 pixels of one (mode, row) line:
+// D = psi' - P o, T = D conj(P) into the CTA's term buffer, nm += D conj(o).
+// PMODE: the probe values from registers (0), a shared-memory row (1) or a
+// global row through L1 (2).  The pointers do not alias, which lets every
+// load be issued ahead of the term stores.
+template <int W, int PMODE>
+PTY_D void upd_terms(const float2* v, const float2* pk, const float2* __restrict__ orow,
+                     const float2* __restrict__ prow, float2* __restrict__ T, float2* nm,
+                     int lane) {
+  using G = Line<W>;
+#pragma unroll
+  for (int n1 = 0; n1 < G::N1; ++n1) {
+    const int c = G::N2 * n1 + lane;
+    const float2 o = orow[c];
+    const float2 pkv = PMODE == 0 ? pk[n1] : PMODE == 1 ? prow[c] : __ldg(prow + c);
+    const float2 D = csub(v[n1], cmul(pkv, o));
+    T[c] = cmulc(D, pkv);
+    nm[n1] = cadd(nm[n1], cmulc(D, o));
+  }
+}
+
+// The object update of the CTA's R rows (Eq. 6, sum of the modes' terms in
+// mode order) and the denominator sums, two pixels per step with their loads
+// issued before either pixel's stores.
+PTY_D void upd_object(int R, int W, int M, const float2* __restrict__ oc,
+                      const float2* __restrict__ tb, const float* __restrict__ invd,
+                      float* __restrict__ den, float2* __restrict__ O, int Hx, int2 cc, int r0,
+                      float2* __restrict__ onew, bool refine, float omb, float bom) {
+  const int n = R * W, st = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < n; e0 += 2 * st) {
+    const bool two = e0 + st < n;
+    float2 o2[2], s2[2];
+    float sc2[2], d2[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 0 || two) {
+        const int e = e0 + h * st, rr = e / W, c = e - rr * W;
+        o2[h] = oc[e];
+        float2 sm = make_float2(0.f, 0.f);
+        for (int kk = 0; kk < M; ++kk) sm = cadd(sm, tb[(kk * R + rr) * W + c]);
+        s2[h] = sm;
+        sc2[h] = invd[e];
+        d2[h] = den[e];
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
+      const int e = e0 + h * st, rr = e / W, c = e - rr * W;
+      const float2 o = o2[h];
+      const float2 onw = make_float2(fmaf(sc2[h], s2[h].x, o.x), fmaf(sc2[h], s2[h].y, o.y));
+      O[(size_t)(cc.x + r0 + rr) * Hx + cc.y + c] = onw;
+      if (refine) onew[e] = onw;
+      den[e] = d2[h] + fmaf(omb, cabs2(o), bom);
+    }
+  }
 }
 
 // The next patch's far-field and crop rows are requested while the current
@@ -580,35 +658,13 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     __syncthreads();  // tbuf is reused below for the D conj(P) terms
     if (own) {
       float2* T = tbuf + (k * R + r) * W;
-#pragma unroll
-      for (int n1 = 0; n1 < G::N1; ++n1) {
-        const int c = G::N2 * n1 + lane;
-        const float2 o = oc[r * W + c];
-        float2 pkv;
-        if constexpr (PK_REG)
-          pkv = pk[n1];
-        else if constexpr (PSTAGE)
-          pkv = prs[(k * R + r) * W + c];
-        else
-          pkv = __ldg(prow + c);
-        const float2 D = csub(v[n1], cmul(pkv, o));
-        T[c] = cmulc(D, pkv);
-        nm[n1] = cadd(nm[n1], cmulc(D, o));
-      }
+      constexpr int PMODE = PK_REG ? 0 : PSTAGE ? 1 : 2;
+      upd_terms<W, PMODE>(v, pk, oc + r * W, PSTAGE ? prs + (k * R + r) * W : prow, T, nm, lane);
     }
     __syncthreads();
     const float om = som[lp - p0];
-    for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
-      const int rr = e / W, c = e - rr * W;
-      const float2 o = oc[e];
-      float2 s = make_float2(0.f, 0.f);
-      for (int kk = 0; kk < M; ++kk) s = cadd(s, tbuf[(kk * R + rr) * W + c]);
-      const float sc = invd[e];
-      const float2 onw = make_float2(fmaf(sc, s.x, o.x), fmaf(sc, s.y, o.y));
-      O[(size_t)(cc.x + r0 + rr) * Hx + cc.y + c] = onw;
-      if (refine) onew[e] = onw;
-      den[e] += fmaf(1.f - a.beta, cabs2(o), a.beta * om);
-    }
+    upd_object(R, W, M, oc, tbuf, invd, den, O, Hx, cc, r0, onew, refine, 1.f - a.beta,
+               a.beta * om);
     osum_local += om;
     // without registration the next patch's first barrier orders these reads
     // of tbuf before its transpose writes
@@ -662,15 +718,35 @@ PTY_D void probe_apply_body(float2* P, int M, int WW, const float2* pnum, const 
   for (int s = 0; s < nslots; ++s) os += osum[s];
   const float guard = reg_eps * os;
   float lmax = 0.f;
+  // The slot sums run in slot order; their loads are issued eight slots at a
+  // time (independent loads in flight instead of one L2 round trip per slot).
+  constexpr int kB = 8;
   for (int pix = bx * blockDim.x + threadIdx.x; pix < WW; pix += gx * blockDim.x) {
     float d = 0.f;
-    for (int s = 0; s < nslots; ++s) d += pden[(size_t)s * WW + pix];
+    for (int s0 = 0; s0 < nslots; s0 += kB) {
+      float dv[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u)
+        dv[u] = s0 + u < nslots ? pden[(size_t)(s0 + u) * WW + pix] : 0.f;
+#pragma unroll
+      for (int u = 0; u < kB; ++u)
+        if (s0 + u < nslots) d += dv[u];
+    }
     const float dd = d + guard;
     const float sc = dd > 0.f ? alpha_P / dd : 0.f;  // zero numerator too
     float pint = 0.f;
     for (int k = 0; k < M; ++k) {
       float2 n = make_float2(0.f, 0.f);
-      for (int s = 0; s < nslots; ++s) n = cadd(n, pnum[((size_t)s * M + k) * WW + pix]);
+      for (int s0 = 0; s0 < nslots; s0 += kB) {
+        float2 nv[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+          nv[u] = s0 + u < nslots ? pnum[((size_t)(s0 + u) * M + k) * WW + pix]
+                                  : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+          if (s0 + u < nslots) n = cadd(n, nv[u]);
+      }
       float2 p = P[(size_t)k * WW + pix];
       p = make_float2(fmaf(sc, n.x, p.x), fmaf(sc, n.y, p.y));
       P[(size_t)k * WW + pix] = p;
