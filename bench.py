@@ -470,6 +470,10 @@ def run_ours(args, wl, rank, world, local):
                         "peak_measured": ffma, "frac_of_measured": achieved / ffma if ffma else None,
                         "peak_measured_source": "FMA-chain kernel (pty_measure_fp32_peak)",
                         "share": kst["ms"][dom] / total_ms},
+           # every pass against the same FP32 roof: each one's algorithmic flops
+           # per pattern update x N / its summed event time
+           "frac_by_kernel": {k: pf[k] * wl.N / (kst["ms"][k] / 1e3) / 1e12 / peak
+                              for k in kinds if k in pf and kst["ms"][k] > 0},
            "kernel_ms": {k: kst["ms"][k] for k in kinds},
            "kernel_launches": {k: kst["launches"][k] for k in kinds},
            "gpu_launches": launches,
