@@ -65,10 +65,11 @@ def per_pass_flops(W, M):
 
 # DRAM bytes per pattern update of each pass, warm L2: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum with --cache-control none on
-# `bench.py --workload spiral_256_n2000` (256^2 x 5 modes; launches 31-60 of
-# the three passes, groups 10-19, 133 patches).  Valid for the pass kernels as
-# profiled; a launch's traffic is this times its patches.
-DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.226e6, "cols": 0.378e6, "rows_inv": 0.096e6}}
+# `bench.py --workload spiral_256_n2000` (256^2 x 5 modes; launches 41-80 of
+# the three passes and the probe update, groups 10-19, 133 patches).  Valid
+# for the pass kernels as profiled; a launch's traffic is this times its
+# patches.
+DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.252e6, "cols": 0.390e6, "rows_inv": 0.104e6}}
 
 
 def fp32_peak_tflops():
