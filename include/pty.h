@@ -192,7 +192,8 @@ int pty_set_adam_state(pty_handle* h, const float* m, const float* v, int t,
  * R rows per CTA of the row passes (M * R * lanes <= 256 threads), ppc
  * patches per CTA of the row passes, CB columns per CTA of the column pass
  * (2, 4, 8 or 16, dividing W/2; M * CB * lanes <= 384 threads), scratch_bytes
- * the far-field chunk budget,
+ * the far-field chunk budget (also the chunk of the differentiable form,
+ * whose per-patch passes take full chunks across its groups),
  * ppcb patches per CTA of the column pass.
  * fused = S > 0 (W <= 128 only) replaces the three passes of the M-rPIE
  * section's per-patch update (Eqs. 1, 2, 4-7) by one kernel per group: a

@@ -1139,26 +1139,34 @@ int grad_run(pty_handle* h, const void* Ov, const void* Pv, const float* pos, fl
     CU(cudaMemsetAsync(h->pnum, 0, sizeof(float2) * h->nslots * h->M * W2, h->stream));
   }
   CU(cudaMemsetAsync(h->err_part, 0, sizeof(float) * h->err_part_n, h->stream));
+  // Nothing is updated during the evaluation, so the per-patch passes take
+  // full chunks of the group-ordered position list regardless of where the
+  // groups end; only the scatter into dL/dO follows the groups (one launch
+  // per group part in the chunk: disjoint boxes, no atomics, a fixed order).
   const int G = (int)h->ggptr.size() - 1;
-  for (int g = 0; g < G; ++g) {
-    const int n = h->ggptr[g + 1] - h->ggptr[g];
-    const int* ids = h->ggpos_d + h->ggptr[g];
-    for (int c0 = 0; c0 < n; c0 += h->Qcg) {
-      const int nc = std::min(h->Qcg, n - c0);
-      const int* idc = ids + c0;
-      pty_handle::Mark m(h, PTY_K_GRAD);
-      CU(pty::launch_grad_rows_fwd(h->tl, O, h->Hx, P, idc, pos, nc, h->tw, h->scratch, npl,
-                                   h->stream));
-      CU(pty::launch_cols_grad(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, delta,
-                               h->err_part, npl, h->tma_b ? &h->tmap_b : nullptr, h->tma_err,
-                               h->stream));
+  const int N = h->ggptr[G];
+  int g = 0;
+  for (int c0 = 0; c0 < N; c0 += h->Qcg) {
+    const int nc = std::min(h->Qcg, N - c0);
+    const int* idc = h->ggpos_d + c0;
+    pty_handle::Mark m(h, PTY_K_GRAD);
+    CU(pty::launch_grad_rows_fwd(h->tl, O, h->Hx, P, idc, pos, nc, h->tw, h->scratch, npl,
+                                 h->stream));
+    CU(pty::launch_cols_grad(h->tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, delta,
+                             h->err_part, npl, h->tma_b ? &h->tmap_b : nullptr, h->tma_err,
+                             h->stream));
+    h->n_launch[PTY_K_GRAD] += 1;
+    if (adjoint) {
+      CU(pty::launch_grad_rows_inv(h->tl, O, h->Hx, P, idc, pos, nc, h->scratch, npl, h->tw,
+                                   h->pnum, 1, h->gpos_part, h->stream));
       h->n_launch[PTY_K_GRAD] += 1;
-      if (adjoint) {
-        CU(pty::launch_grad_rows_inv(h->tl, O, h->Hx, P, idc, pos, nc, h->scratch, npl, h->tw,
-                                     h->pnum, 1, h->gpos_part, h->stream));
-        CU(pty::launch_grad_scatter(h->W, h->M, gO, h->Hx, idc, pos, nc, h->scratch, npl,
+      for (; g < G && h->ggptr[g] < c0 + nc; ++g) {
+        const int a = std::max(h->ggptr[g], c0), b = std::min(h->ggptr[g + 1], c0 + nc);
+        CU(pty::launch_grad_scatter(h->W, h->M, gO, h->Hx, h->ggpos_d + a, pos, b - a,
+                                    h->scratch + (size_t)(a - c0) * npl * W2, npl,
                                     h->stream));
-        h->n_launch[PTY_K_GRAD] += 2;
+        h->n_launch[PTY_K_GRAD] += 1;
+        if (h->ggptr[g + 1] > c0 + nc) break;  // the group continues in the next chunk
       }
     }
   }
@@ -1397,13 +1405,17 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   const size_t budget = t->scratch_bytes ? t->scratch_bytes : ((size_t)64 << 20);
   const int Qc = (int)std::min<size_t>((size_t)h->N, std::max<size_t>(1, budget / (W2 * M * sizeof(float2))));
   const int Qcr = Qc;
+  // the differentiable form's chunk (M far-field planes and the crop
+  // gradient per patch) under the same budget
+  const int Qcg = (int)std::min<size_t>((size_t)h->N,
+                                        std::max<size_t>(1, budget / (W2 * (M + 1) * sizeof(float2))));
   // grow the buffers whose size depends on the tiling
   // slots for this ppc and for the default ppc (4) the batched form uses
   const int ppc_min = std::min(std::min(nt.ppc, nr.ppc), 4);
-  const int nslots = std::max((std::max(std::max(Qc, Qcr), h->Qcg) + ppc_min - 1) / ppc_min,
+  const int nslots = std::max((std::max(std::max(Qc, Qcr), Qcg) + ppc_min - 1) / ppc_min,
                               npg.ncap);  // the fused kernel: one slot per cluster
   const size_t scratch = std::max(std::max((size_t)Qc * M, (size_t)Qcr * nr.npl),
-                                  (size_t)h->Qcg * (M + 1)) * W2;
+                                  (size_t)Qcg * (M + 1)) * W2;
   const size_t cur_scratch = std::max(std::max((size_t)h->Qc * M, (size_t)h->Qcr * h->tlr.npl),
                                       (size_t)h->Qcg * (M + 1)) * W2;
   CU(cudaStreamSynchronize(h->stream));
@@ -1443,6 +1455,7 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   remap_scratch(h);
   h->Qc = Qc;
   h->Qcr = Qcr;
+  h->Qcg = Qcg;
   h->err_part_n = (size_t)h->N * (W / nt.CB);
   ++h->epoch;
   CU(pty::set_smem_limits(h->tl));
