@@ -468,11 +468,36 @@ pty::UpdArgs upd_args(const pty_rpie_params* p) {
   return pty::UpdArgs{p->alpha_O, p->alpha_P, p->beta, p->gamma, p->eps, p->reg_eps};
 }
 
-// refine: 0 = plain, 1 = XCORR_A, 2 = XCORR_B registration of every patch
+// Registration (mode 1 XCORR_A, 2 XCORR_B) of patches [b0, b0 + nb) of the
+// current grouping, whose crop planes the passes left in scratch patch slots
+// 0 .. nb - 1 (planes M, M + 1 of the registration tiling).
+int run_registration(pty_handle* h, int b0, int nb, int mode) {
+  if (nb <= 0 || mode == 0) return PTY_OK;
+  const int* ids = h->gpos_d + b0;
+  const int npl = h->tlr.npl;
+  pty_handle::Mark m(h, PTY_K_REFINE);
+  if (mode == 2) {
+    CU(pty::launch_xcorrb_rows(h->rg, h->scratch, npl, h->M, nb, h->tw, h->stream));
+    h->n_launch[PTY_K_REFINE] += 1;
+  }
+  CU(pty::launch_xcorr_cols(h->rg, h->scratch, npl, h->M, nb, h->tw, h->stream));
+  CU(pty::launch_xcorr_rows(h->rg, h->scratch, npl, h->M, nb, h->tw, h->cval, h->cidx,
+                            h->stream));
+  CU(pty::launch_updft(h->rg, h->scratch, npl, h->M, ids, nb, h->cval, h->cidx, h->roots,
+                       h->upart, h->shift, h->gap, h->updone, h->tma_err, h->stream));
+  h->n_launch[PTY_K_REFINE] += 2;
+  return PTY_OK;
+}
+
+// refine: 0 = plain, 1 = XCORR_A, 2 = XCORR_B registration of every patch.
+// boff >= 0 (refining): the group is one chunk whose planes sit in scratch
+// patch slots boff .. boff + n - 1, and its registration is left to the
+// caller (run_registration over a batch of consecutive groups); boff < 0:
+// chunks of the scratch budget, each registered at once.
 // One group on the fused patch kernel: without registration the whole group
 // in one launch (no scratch), with it in chunks of the registration's scratch
 // planes, each chunk followed by the registration kernels.
-int run_group_fused(pty_handle* h, int g, const pty_rpie_params* p, int refine) {
+int run_group_fused(pty_handle* h, int g, const pty_rpie_params* p, int refine, int boff) {
   const int n = h->gptr[g + 1] - h->gptr[g];
   const int* ids = h->gpos_d + h->gptr[g];
   const pty::Tiling& tl = refine ? h->tlr : h->tl;
@@ -483,7 +508,8 @@ int run_group_fused(pty_handle* h, int g, const pty_rpie_params* p, int refine) 
   a.pmax_part = h->pmax_part; a.n_pmax = h->tl.n_pmax;
   a.pnum = h->pnum; a.pden = h->pden; a.osum = h->osum;
   a.err_part = h->err_part; a.nb = h->W / tl.CB;  // the stride the error reduction reads
-  a.scratch = h->scratch; a.npl = tl.npl; a.refine = refine;
+  a.scratch = h->scratch + (boff > 0 ? (size_t)boff * tl.npl * h->W * h->W : 0);
+  a.npl = tl.npl; a.refine = refine;
   int used = 0;
   for (int c0 = 0; c0 < n; c0 += Qc) {
     const int nc = std::min(Qc, n - c0);
@@ -497,7 +523,7 @@ int run_group_fused(pty_handle* h, int g, const pty_rpie_params* p, int refine) 
       pty_handle::Mark m(h, PTY_K_PATCH);
       CU(pty::launch_patch(h->pg, a, ncl, h->stream));
     }
-    if (refine) {
+    if (refine && boff < 0) {
       pty_handle::Mark m(h, PTY_K_REFINE);
       if (refine == 2) {
         CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
@@ -521,35 +547,38 @@ int run_group_fused(pty_handle* h, int g, const pty_rpie_params* p, int refine) 
   return PTY_OK;
 }
 
-int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0) {
-  if (h->pg.S > 0) return run_group_fused(h, g, p, refine);
+int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0, int boff = -1) {
+  if (h->pg.S > 0) return run_group_fused(h, g, p, refine, boff);
   const int n = h->gptr[g + 1] - h->gptr[g];
   const int* ids = h->gpos_d + h->gptr[g];
   const pty::UpdArgs a = upd_args(p);
   const pty::Tiling& tl = refine ? h->tlr : h->tl;
   const int Qc = refine ? h->Qcr : h->Qc;
+  // the batch slot of the group's first patch (its planes in the scratch)
+  const int p0 = boff > 0 ? boff : 0;
+  float2* scr = h->scratch + (size_t)p0 * tl.npl * h->W * h->W;
   for (int c0 = 0; c0 < n; c0 += Qc) {
     const int nc = std::min(Qc, n - c0);
     const int* idc = ids + c0;
     {
       pty_handle::Mark m(h, PTY_K_ROWS_FWD);
-      CU(pty::launch_rows_fwd(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, h->scratch,
+      CU(pty::launch_rows_fwd(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, scr,
                               h->omax_part, h->stream));
     }
     {
       pty_handle::Mark m(h, PTY_K_COLS);
-      CU(pty::launch_cols(tl, h->scratch, h->I, idc, nc, h->tw, h->inv_w, p->eps,
+      CU(pty::launch_cols(tl, scr, h->I, idc, nc, h->tw, h->inv_w, p->eps,
                           h->err_part,
                           refine ? (h->tma_br ? &h->tmap_br : nullptr) : (h->tma_b ? &h->tmap_b : nullptr),
-                          h->tma_err, h->stream, refine == 2 ? h->M : -1));
+                          h->tma_err, h->stream, refine == 2 ? h->M : -1, p0 * tl.npl));
     }
     {
       pty_handle::Mark m(h, PTY_K_ROWS_INV);
-      CU(pty::launch_rows_inv(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->scratch,
+      CU(pty::launch_rows_inv(tl, h->O, h->Hx, h->P, idc, h->corners, nc, scr,
                               h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
                               c0 > 0, h->tma_err, h->stream, refine == 1 ? 1 : 0));
     }
-    if (refine) {
+    if (refine && boff < 0) {
       pty_handle::Mark m(h, PTY_K_REFINE);
       if (refine == 2) {
         CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
@@ -1059,7 +1088,31 @@ int pty_refine_positions(pty_handle* h, int n_iter, const pty_rpie_params* p,
     if (on) CU(pty::set_smem_limits(h->tlr));
     const int G = (int)h->gptr.size() - 1;
     const int mode = on ? (r->point == PTY_XCORR_B ? 2 : 1) : 0;
-    for (int g = 0; g < G; ++g) TRY(run_group(h, g, p, mode));
+    // The registration of a group changes nothing the later groups read (the
+    // positions move at the end of the iteration), so it runs once per batch
+    // of consecutive groups: patches [b0, b0 + nb) of the grouping, their
+    // crop planes in scratch patch slots 0 .. nb - 1.
+    int b0 = 0, nb = 0;
+    for (int g = 0; g < G; ++g) {
+      const int n = h->gptr[g + 1] - h->gptr[g];
+      if (mode == 0) {
+        TRY(run_group(h, g, p, 0));
+        continue;
+      }
+      if (nb + n > h->Qcr) {  // the batch is full
+        TRY(run_registration(h, b0, nb, mode));
+        b0 = h->gptr[g];
+        nb = 0;
+      }
+      if (n > h->Qcr) {  // a group larger than the scratch: chunks, each registered at once
+        TRY(run_group(h, g, p, mode));
+        b0 = h->gptr[g + 1];
+        continue;
+      }
+      TRY(run_group(h, g, p, mode, nb));
+      nb += n;
+    }
+    TRY(run_registration(h, b0, nb, mode));
     {
       // the partial sums of this iteration follow its column-pass tiling
       const size_t nerr = (size_t)h->N * (h->W / (on ? h->tlr.CB : h->tl.CB));

@@ -71,11 +71,12 @@ cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx,
 // tm (may be NULL): tensor map of the scratch for TMA staging (see
 // encode_far_field_map); a TMA wait that times out sets *err.  xb >= 0
 // (XCORR_B): also write the model intensity and the counts into scratch
-// planes xb, xb + 1.
+// planes xb, xb + 1.  plane0: the plane of the tensor map at which `scratch`
+// starts (a chunk placed further into the scratch).
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
                         float eps, float* err_part, const CUtensorMap* tm, int* err,
-                        cudaStream_t s, int xb = -1);
+                        cudaStream_t s, int xb = -1, int plane0 = 0);
 // Fourier-domain step of the gradient (amplitude loss, delta-smoothed).
 cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I,
                              const int* ids, int npatch, const float2* tw, float inv_w,

@@ -180,12 +180,13 @@ PTY_D void rows_fwd_body(const float2* O, int Hx, const float2* P,
 template <int W, int CB>
 PTY_D void cols_stage(const float2* scratch, const uint16_t* I, int j, int lp, int npl, int MA,
                       int c0, float2* stage, uint16_t* cnt, const void* tm,
-                      unsigned long long* mbar) {
+                      unsigned long long* mbar, int plane0 = 0) {
   if (tm) {
     if (threadIdx.x == 0) {
       fence_proxy_async();  // the stage was just read through the generic proxy
       mbar_expect_tx(mbar, (unsigned)(MA * W * CB * sizeof(float2)));
-      for (int k = 0; k < MA; ++k) tma_load_3d(stage + k * W * CB, tm, c0, 0, lp * npl + k, mbar);
+      for (int k = 0; k < MA; ++k)
+        tma_load_3d(stage + k * W * CB, tm, c0, 0, plane0 + lp * npl + k, mbar);
     }
   } else {
     const int cpr = CB / 2;  // 16-byte chunks per row segment
@@ -249,7 +250,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
        float* __restrict__ err_part, int npl, int ppcb, int npatch, int bx, int by,
-       const void* tm = nullptr, int* err = nullptr, int xb = -1) {
+       const void* tm = nullptr, int* err = nullptr, int xb = -1, int plane0 = 0) {
   using G = Line<W>;
   extern __shared__ float4 smem4[];
   __shared__ __align__(8) unsigned long long mbar;
@@ -282,7 +283,8 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
   pdl_wait();  // the far field comes from pass A
   __syncthreads();
   if constexpr (STAGE) {
-    if (p0 < p1) cols_stage<W, CB>(scratch, I, sids[0], p0, npl, M, c0, stage, cnt, tm, &mbar);
+    if (p0 < p1)
+      cols_stage<W, CB>(scratch, I, sids[0], p0, npl, M, c0, stage, cnt, tm, &mbar, plane0);
     cp_async_commit();
   }
   for (int lp = p0; lp < p1; ++lp) {
@@ -324,7 +326,7 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
       }
       if (lp + 1 < p1)
         cols_stage<W, CB>(scratch, I, sids[lp + 1 - p0], lp + 1, npl, M, c0, stage,
-                          cnt + ((lp + 1 - p0) & 1) * W * CB, tm, &mbar);
+                          cnt + ((lp + 1 - p0) & 1) * W * CB, tm, &mbar, plane0);
       cp_async_commit();
     } else {
       // the counts and the columns are requested together: one round trip

@@ -38,9 +38,9 @@ k_cols(float2* __restrict__ scratch, int M,
        const uint16_t* __restrict__ I, const int* __restrict__ ids,
        const float2* __restrict__ tw_g, float inv_w, float eps,
        float* __restrict__ err_part, int npl, int ppcb, int npatch,
-       const __grid_constant__ CUtensorMap tmap, int use_tma, int* err, int xb) {
+       const __grid_constant__ CUtensorMap tmap, int use_tma, int* err, int xb, int plane0) {
   cols_body<W, CB, GRAD>(scratch, M, I, ids, tw_g, inv_w, eps, err_part, npl, ppcb, npatch,
-                         blockIdx.x, blockIdx.y, use_tma ? &tmap : nullptr, err, xb);
+                         blockIdx.x, blockIdx.y, use_tma ? &tmap : nullptr, err, xb, plane0);
 }
 
 template <int W, bool PSTAGE>
@@ -505,7 +505,7 @@ cudaError_t launch_rows_fwd_plain(const Tiling& t, const float2* O, int Hx, cons
 cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                         const int* ids, int npatch, const float2* tw, float inv_w,
                         float eps, float* err_part, const CUtensorMap* tm, int* err,
-                        cudaStream_t s, int xb) {
+                        cudaStream_t s, int xb, int plane0) {
   if (npatch <= 0) return cudaSuccess;
   dim3 grid(t.W / t.CB, (npatch + t.ppcb - 1) / t.ppcb);
   cudaError_t e = cudaSuccess;
@@ -515,12 +515,12 @@ cudaError_t launch_cols(const Tiling& t, float2* scratch, const uint16_t* I,
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, eps, err_part,
                                                            t.npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err, xb)
+                                                           tm ? *tm : none, tm ? 1 : 0, err, xb, plane0)
                                                     : launch_pdl(k_cols<WW, CBB, false, false>,
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, eps, err_part,
                                                            t.npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err, xb)));
+                                                           tm ? *tm : none, tm ? 1 : 0, err, xb, plane0)));
   return e;
 }
 
@@ -537,12 +537,12 @@ cudaError_t launch_cols_grad(const Tiling& t, float2* scratch, const uint16_t* I
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, delta,
                                                            loss_part, npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err, -1)
+                                                           tm ? *tm : none, tm ? 1 : 0, err, -1, 0)
                                                     : launch_pdl(k_cols<WW, CBB, true, false>,
                                                            grid, dim3(t.thrB), t.smB, s, scratch,
                                                            t.M, I, ids, tw, inv_w, delta,
                                                            loss_part, npl, t.ppcb, npatch,
-                                                           tm ? *tm : none, tm ? 1 : 0, err, -1)));
+                                                           tm ? *tm : none, tm ? 1 : 0, err, -1, 0)));
   return e;
 }
 
