@@ -476,8 +476,11 @@ int run_registration(pty_handle* h, int b0, int nb, int mode) {
   const int* ids = h->gpos_d + b0;
   const int npl = h->tlr.npl;
   pty_handle::Mark m(h, PTY_K_REFINE);
-  if (mode == 2) {
-    CU(pty::launch_xcorrb_rows(h->rg, h->scratch, npl, h->M, nb, h->tw, h->stream));
+  if (mode == 2 || h->pg.S == 0) {
+    // XCORR_B: both detector-plane images; XCORR_A on the three passes: the
+    // refined crop, which pass C stores untransformed
+    CU(pty::launch_xcorrb_rows(h->rg, h->scratch, npl, mode == 2 ? h->M : h->M + 1,
+                               mode == 2 ? 2 : 1, nb, h->tw, h->stream));
     h->n_launch[PTY_K_REFINE] += 1;
   }
   CU(pty::launch_xcorr_cols(h->rg, h->scratch, npl, h->M, nb, h->tw, h->stream));
@@ -526,7 +529,7 @@ int run_group_fused(pty_handle* h, int g, const pty_rpie_params* p, int refine, 
     if (refine && boff < 0) {
       pty_handle::Mark m(h, PTY_K_REFINE);
       if (refine == 2) {
-        CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
+        CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, h->M, 2, nc, h->tw, h->stream));
         h->n_launch[PTY_K_REFINE] += 1;
       }
       CU(pty::launch_xcorr_cols(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
@@ -580,8 +583,11 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0, in
     }
     if (refine && boff < 0) {
       pty_handle::Mark m(h, PTY_K_REFINE);
-      if (refine == 2) {
-        CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));
+      {
+        // XCORR_B: both detector-plane images; XCORR_A: the refined crop,
+        // which pass C stores untransformed
+        CU(pty::launch_xcorrb_rows(h->rg, h->scratch, tl.npl, refine == 2 ? h->M : h->M + 1,
+                                   refine == 2 ? 2 : 1, nc, h->tw, h->stream));
         h->n_launch[PTY_K_REFINE] += 1;
       }
       CU(pty::launch_xcorr_cols(h->rg, h->scratch, tl.npl, h->M, nc, h->tw, h->stream));

@@ -147,9 +147,11 @@ RefGeo make_refgeo(int W, int U, bool tc = true);
 cudaError_t set_refine_smem(const RefGeo& g);
 // roots exp(+2 pi i n / (U W)), n = 0..U W - 1 (host, double -> float)
 void make_up_roots(int W, int U, float2* out);
-// XCORR_B: forward row DFTs of planes M, M + 1 (model intensity, counts).
-cudaError_t launch_xcorrb_rows(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
-                               const float2* tw, cudaStream_t s);
+// Forward row DFTs, in place, of planes plane .. plane + nplanes - 1 of every
+// patch: XCORR_B's model intensity and counts (planes M, M + 1), XCORR_A's
+// refined crop (plane M + 1) as the three-pass path leaves it.
+cudaError_t launch_xcorrb_rows(const RefGeo& g, float2* scratch, int npl, int plane,
+                               int nplanes, int npatch, const float2* tw, cudaStream_t s);
 cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
                               const float2* tw, cudaStream_t s);
 cudaError_t launch_xcorr_rows(const RefGeo& g, const float2* scratch, int npl, int M,

@@ -560,8 +560,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   float2* tw = reinterpret_cast<float2*>(smem4);
   float2* tbuf = tw + W;             // transpose buffer, then D conj(P) terms
   float2* ostash = tbuf + TB;        // 2 x R x W: crop rows, double-buffered
-  float2* onew = ostash + 2 * R * W; // refined crop rows (refine only)
-  float2* zst = onew + (refine ? R * W : 0);  // M x R x W far-field rows
+  float2* zst = ostash + 2 * R * W;  // M x R x W far-field rows
   float2* prs = zst + M * R * W;     // M x R x W probe rows (PSTAGE only)
   float* invd = reinterpret_cast<float*>(prs + (PSTAGE ? M * R * W : 0));  // alpha_O / den.
   float* den = invd + R * W;
@@ -665,30 +664,14 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     }
     __syncthreads();
     const float om = som[lp - p0];
-    upd_object(R, W, M, oc, tbuf, invd, den, O, Hx, cc, r0, onew, refine, 1.f - a.beta,
-               a.beta * om);
+    // with XCORR_A the refined crop rows o'_j go, untransformed, to plane
+    // M + 1 (the registration takes their row DFTs for a batch of groups)
+    upd_object(R, W, M, oc, tbuf, invd, den, O, Hx, cc, r0,
+               refine ? scratch + (((size_t)lp * npl + M + 1) * W + r0) * W : nullptr, refine,
+               1.f - a.beta, a.beta * om);
     osum_local += om;
-    // without registration the next patch's first barrier orders these reads
-    // of tbuf before its transpose writes
-    if (refine) {
-      __syncthreads();  // onew
-      // forward row DFTs of the refined crop o'_j -> plane M + 1 (XCORR_A)
-      if (line < R && lane < G::N2) {
-        float2 v2[G::N1];
-#pragma unroll
-        for (int n1 = 0; n1 < G::N1; ++n1) v2[n1] = onew[line * W + G::N2 * n1 + lane];
-        fwd_step1<W>(v2, lane, tw, tbuf + line * G::LP);
-      }
-      __syncthreads();
-      if (line < R && lane < G::N1) {
-        float2 zz[G::N2];
-        fwd_step3<W>(zz, lane, tbuf + line * G::LP);
-        float2* dst = scratch + (((size_t)lp * npl + M + 1) * W + r0 + line) * W;
-#pragma unroll
-        for (int k2 = 0; k2 < G::N2; ++k2) dst[lane + G::N1 * k2] = zz[k2];
-      }
-      __syncthreads();
-    }
+    // the next patch's first barrier orders these reads of tbuf before its
+    // transpose writes
   }
   cp_async_wait<0>();
   const int slot = by;

@@ -137,10 +137,12 @@ k_xcorr_cols(float2* __restrict__ scratch, int npl, int M, int CB,
 }
 
 // ------------------------------------------------------------ xcorrb_rows
-// XCORR_B: forward row DFTs of the two real images pass B left in planes M
-// (model intensity) and M + 1 (counts); the correlation passes then take
-// them exactly as they take the two crops' row DFTs for XCORR_A.  The two
-// planes are consecutive, so a CTA's RX lines are rows of a 2W-row block.
+// Forward row DFTs, in place, of consecutive planes starting at plane M (the
+// kernel's M): XCORR_B's two real images pass B left in planes M (model
+// intensity) and M + 1 (counts), or XCORR_A's refined crop, which pass C
+// leaves untransformed in plane M + 1.  The correlation passes then take them
+// as they take the crops' row DFTs.  A CTA's RX lines are rows of the block
+// of consecutive planes.
 template <int W>
 __global__ void __launch_bounds__(256)
 k_xcorrb_rows(float2* __restrict__ scratch, int npl, int M, int RX,
@@ -151,7 +153,7 @@ k_xcorrb_rows(float2* __restrict__ scratch, int npl, int M, int RX,
   float2* tbuf = tw + W;
   pdl_trigger();
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
-  pdl_wait();  // both images come from the column pass
+  pdl_wait();  // the images come from the column pass (XCORR_B) or pass C (XCORR_A)
   __syncthreads();
   const int lp = blockIdx.y, r0 = blockIdx.x * RX;
   const int line = threadIdx.x / G::L, lane = threadIdx.x - line * G::L;
@@ -811,15 +813,15 @@ cudaError_t launch_xcorr_cols(const RefGeo& g, float2* scratch, int npl, int M, 
   return e;
 }
 
-cudaError_t launch_xcorrb_rows(const RefGeo& g, float2* scratch, int npl, int M, int npatch,
-                               const float2* tw, cudaStream_t s) {
+cudaError_t launch_xcorrb_rows(const RefGeo& g, float2* scratch, int npl, int plane,
+                               int nplanes, int npatch, const float2* tw, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   PTY_DISPATCH_W(g.W, {
     using G = Line<WW>;
     const int thr = (g.RX * G::L + 31) / 32 * 32;
-    e = launch_pdl(k_xcorrb_rows<WW>, dim3(2 * WW / g.RX, npatch), dim3(thr), g.smR, s, scratch,
-                   npl, M, g.RX, tw);
+    e = launch_pdl(k_xcorrb_rows<WW>, dim3(nplanes * WW / g.RX, npatch), dim3(thr), g.smR, s,
+                   scratch, npl, plane, g.RX, tw);
   });
   return e;
 }

@@ -435,7 +435,7 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
           128;                        // alignment of the stage
   t.smI = (size_t)(W + M * CB * LP) * sizeof(float2) + (size_t)M * CB * W * sizeof(float);
   const int TB = std::max(M * R * LP, M * R * W);
-  const size_t smC0 = (size_t)(W + TB + 2 * R * W + (refine ? R * W : 0) + M * R * W) *
+  const size_t smC0 = (size_t)(W + TB + 2 * R * W + M * R * W) *
                           sizeof(float2) +
                       (size_t)2 * R * W * sizeof(float) + (size_t)t.ppc * (sizeof(int2) + sizeof(float));
   const size_t smC1 = smC0 + (size_t)M * R * W * sizeof(float2);
