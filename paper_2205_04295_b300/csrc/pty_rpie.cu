@@ -65,6 +65,80 @@ k_probe_apply(float2* __restrict__ P, int M, int WW, const float2* __restrict__ 
   probe_apply_body(P, M, WW, pnum, pden, osum, nslots, alpha_P, reg_eps, pmax_part, blockIdx.x, gridDim.x);
 }
 
+// Probe update of the per-pass path, one thread per (pixel, mode): block
+// (kPaX pixels, M modes), grid n_pmax blocks of WW / n_pmax pixels each.  A
+// thread's slot sums (denominator and its mode's numerator, slot order)
+// load eight slots at a time, both sums' loads in flight together; the new
+// probe intensity sum_k |P_k|^2 of a pixel is added in mode order through
+// shared memory and the block's maximum goes to pmax_part[block].  The same
+// arithmetic as probe_apply_body, which the batched form keeps.
+constexpr int kPaX = 128;
+__global__ void __launch_bounds__(1024)
+k_probe_apply_pm(float2* __restrict__ P, int M, int WW, const float2* __restrict__ pnum,
+                 const float* __restrict__ pden, const float* __restrict__ osum, int nslots,
+                 float alpha_P, float reg_eps, float* __restrict__ pmax_part) {
+  __shared__ float pint_s[8][kPaX];
+  __shared__ float red[32];
+  pdl_trigger();
+  pdl_wait();
+  const int x = threadIdx.x, k = threadIdx.y;
+  float os = 0.f;
+  for (int s = 0; s < nslots; ++s) os += osum[s];
+  const float guard = reg_eps * os;
+  const int ppb = (WW + gridDim.x - 1) / gridDim.x;  // pixels of this block
+  float lmax = 0.f;
+  constexpr int kB = 8;
+  for (int i0 = 0; i0 < ppb; i0 += kPaX) {
+    const int pix = blockIdx.x * ppb + i0 + x;
+    const bool on = i0 + x < ppb && pix < WW;
+    if (on) {
+      float d = 0.f;
+      float2 n = make_float2(0.f, 0.f);
+      for (int s0 = 0; s0 < nslots; s0 += kB) {
+        float dv[kB];
+        float2 nv[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const bool in = s0 + u < nslots;
+          dv[u] = in ? pden[(size_t)(s0 + u) * WW + pix] : 0.f;
+          nv[u] = in ? pnum[((size_t)(s0 + u) * M + k) * WW + pix] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          if (s0 + u < nslots) {
+            d += dv[u];
+            n = cadd(n, nv[u]);
+          }
+        }
+      }
+      const float dd = d + guard;
+      const float sc = dd > 0.f ? alpha_P / dd : 0.f;  // zero numerator too
+      float2 p = P[(size_t)k * WW + pix];
+      p = make_float2(fmaf(sc, n.x, p.x), fmaf(sc, n.y, p.y));
+      P[(size_t)k * WW + pix] = p;
+      pint_s[k][x] = cabs2(p);
+    }
+    __syncthreads();
+    if (on && k == 0) {
+      float pint = 0.f;
+      for (int kk = 0; kk < M; ++kk) pint += pint_s[kk][x];
+      lmax = fmaxf(lmax, pint);
+    }
+    __syncthreads();
+  }
+  // the mode-0 threads are the first kPaX / 32 warps (linear index x + kPaX k)
+  if (k == 0) {
+    const float m = warp_max(lmax);
+    if ((x & 31) == 0) red[x >> 5] = m;
+  }
+  __syncthreads();
+  if (x == 0 && k == 0) {
+    float m = 0.f;
+    for (int i = 0; i < kPaX / 32; ++i) m = fmaxf(m, red[i]);
+    pmax_part[blockIdx.x] = m;
+  }
+}
+
 __global__ void __launch_bounds__(256)
 k_pmax(const float2* __restrict__ P, int M, int WW, float* __restrict__ pmax_part) {
   __shared__ float red[32];
@@ -571,6 +645,9 @@ cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
                                const float* pden, const float* osum, int nslots,
                                float alpha_P, float reg_eps, float* pmax_part,
                                cudaStream_t s) {
+  if (t.M <= 8)
+    return launch_pdl(k_probe_apply_pm, dim3(t.n_pmax), dim3(kPaX, t.M), 0, s, P, t.M,
+                      t.W * t.W, pnum, pden, osum, nslots, alpha_P, reg_eps, pmax_part);
   return launch_pdl(k_probe_apply, dim3(t.n_pmax), dim3(256), 0, s, P, t.M, t.W * t.W, pnum,
                     pden, osum, nslots, alpha_P, reg_eps, pmax_part);
 }
