@@ -390,32 +390,30 @@ PTY_D void updft_finish(int lp, int j, int sy, int sx, int nblocks, int U, int K
 // the 128 x 128 FP32 accumulator in TMEM holds [hi-hi + lo-hi | hi-lo]
 // products, added at read-out.
 //
-// Pipeline over chunks of 16 columns of X: X is staged by cp.async two
-// chunks ahead; a chunk is split into four K-major planes (Xr hi, Xr lo,
-// Xi hi, Xi lo) and the matching chunk of the two stacked E_c operands into
-// two more, in one of two plane buffers; one thread issues the chunk's 8
+// Pipeline over chunks of 16 columns of X: each thread loads its 8 values of
+// the next chunk into registers while the current one is split; a chunk is
+// split into four K-major planes (Xr hi, Xr lo, Xi hi, Xi lo) and the
+// matching chunk of the two stacked E_c operands into two more, in one of
+// two plane buffers (96 KB: two CTAs per SM, whose phases interleave); one thread issues the chunk's 8
 // MMAs and commits them to that buffer's mbarrier, and the CTA goes on to
 // split the next chunk into the other buffer while they run (a buffer is
 // refilled once its mbarrier says the MMAs that read it are done; every
 // wait is bounded).  The phases exp(2 pi i n / (U W)) come from the root
-// table, staged into shared memory before the dependency wait; their indices
-// are stepped in 32-bit integers.  The block's share E_r[:, rows] T (K x K)
+// table through L1; their indices are stepped in 32-bit integers.  The block's share E_r[:, rows] T (K x K)
 // is then taken on the FP32 cores (2 x 2 outputs per thread) from T copied
 // to shared memory, and updft_final adds the shares.  Rows past W (W < 128,
 // or the second tile at W = 192) are zero.
 constexpr int kTcRows = 128;                  // M of the MMA: rows of X per CTA
 constexpr int kTcKc = 16;                     // columns of X (index v) per chunk
 constexpr int kTcN = 32;                      // fine-grid points held (K <= 32)
-constexpr int kTcRawPitch = kTcKc + 2;        // complex per staged row (144 B)
 constexpr int kTcTPitch = kTcN + 1;           // complex per row of T in shared memory
 constexpr int kTcAPlane = kTcRows * kTcKc * 4;    // bytes of one A plane (128 x 16)
 constexpr int kTcBPlane = 4 * kTcN * kTcKc * 4;   // bytes of one stacked B plane (128 x 16)
 constexpr int kTcBuf = 4 * kTcAPlane + 2 * kTcBPlane;  // one set of operand planes
 constexpr int kTcSBO = (kTcKc / 4) * 128;         // bytes between 8-row groups
-constexpr int kTcRaw = 2 * kTcRows * kTcRawPitch * 8;
-constexpr int kTcFixed = kTcRaw + 2 * kTcBuf + 128;  // + the root table
-static_assert(kTcRows * kTcTPitch * 8 <= kTcRaw, "T reuses the staging buffers");
-static_assert(kTcN * kTcRows * 8 <= 2 * kTcBuf, "E_r reuses the operand planes");
+constexpr int kTcFixed = 2 * kTcBuf + 128;  // two plane buffers: two CTAs per SM
+static_assert(kTcRows * kTcTPitch * 8 <= kTcBuf, "T reuses the second plane buffer");
+static_assert(kTcN * kTcRows * 8 <= kTcBuf, "E_r reuses the first plane buffer");
 
 // Byte offset of element (row, k) in a K-major, no-swizzle plane of kTcKc
 // columns: core matrices (8 rows x 4 values, 128 bytes) with the K-adjacent
@@ -436,7 +434,7 @@ __device__ __forceinline__ void split4(const float* x, float4& hi, float4& lo) {
 }
 
 template <int W>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
 k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
            const float* __restrict__ cval, const int* __restrict__ cidx,
            const float2* __restrict__ roots_g, int U, int K, float2* __restrict__ part,
@@ -449,10 +447,9 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   __shared__ int ri[32];
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem4) + 127) &
                                        ~static_cast<uintptr_t>(127));
-  float2* raw = reinterpret_cast<float2*>(base);   // 2 x [128][kTcRawPitch]
-  char* pl = base + kTcRaw;                         // 2 x (Xr hi, Xr lo, Xi hi, Xi lo, B1, B2)
-  float2* roots = reinterpret_cast<float2*>(pl + 2 * kTcBuf);  // U W roots
-  float2* T = raw;                                  // [128][kTcTPitch] after the MMAs
+  char* pl = base;                                  // 2 x (Xr hi, Xr lo, Xi hi, Xi lo, B1, B2)
+  const float2* roots = roots_g;                    // U W roots, read through L1
+  float2* T = reinterpret_cast<float2*>(pl + kTcBuf);  // [128][kTcTPitch] after the MMAs
   float2* Er = reinterpret_cast<float2*>(pl);       // [K][128] after the MMAs
 
   const int lp = blockIdx.y, u0 = blockIdx.x * kTcRows;
@@ -468,26 +465,23 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
   }
-  // the root table does not depend on earlier kernels: staged before the wait
-  for (int i = tid; i < UW / 2; i += blockDim.x) cp_async<16>(roots + 2 * i, roots_g + 2 * i);
-  cp_async_commit();
-  // rows past W stay zero in both staging buffers
-  const int zr = (kTcRows - nrows) * kTcRawPitch;
-  for (int i = tid; i < 2 * zr; i += blockDim.x)
-    raw[(i / zr) * kTcRows * kTcRawPitch + nrows * kTcRawPitch + i % zr] = make_float2(0.f, 0.f);
   pdl_wait();  // X and the coarse peaks come from the correlation passes
-  auto stage = [&](int c) {
-    if (c < nch) {
-      float2* dst = raw + (c & 1) * kTcRows * kTcRawPitch;
-      for (int i = tid; i < nrows * (kTcKc / 2); i += blockDim.x) {
-        const int r = i / (kTcKc / 2), h = i - r * (kTcKc / 2);
-        cp_async<16>(dst + r * kTcRawPitch + 2 * h, X + (size_t)r * W + c * kTcKc + 2 * h);
-      }
-    }
-    cp_async_commit();  // one group per chunk, empty past the last
+  // A thread's X values of a chunk: row m = tid mod 128, the chunk's columns
+  // 4q .. 4q + 3 for q = 2 (tid / 128) + 0, 1 (8 complex, contiguous; zero past
+  // the last row), loaded into registers one chunk ahead.
+  const int xm = tid & (kTcRows - 1);
+  const bool xrow = xm < nrows;
+  const float4* xsrc = reinterpret_cast<const float4*>(X + (size_t)(xrow ? xm : 0) * W +
+                                                       8 * (tid >> 7));
+  // two chunks ahead: X comes from HBM (a batch's planes exceed L2)
+  float4 xn[4], xn2[4];
+  auto fetch = [&](float4* dst, int c) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      dst[i] = (c < nch && xrow) ? __ldcs(xsrc + c * (kTcKc / 2) + i) : make_float4(0.f, 0.f, 0.f, 0.f);
   };
-  stage(0);
-  stage(1);
+  fetch(xn, 0);
+  fetch(xn2, 1);
   int sy, sx;
   coarse_peak(cval, cidx, lp, nparts, W, sy, sx, rv, ri);  // contains barriers
   tc_fence_after_sync();
@@ -497,6 +491,25 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   // (a warp covers 8 consecutive kq and the 4 column groups: conflict-free)
   const int kq = 8 * (warp & 3) + (tid & 7), vq = 4 * ((tid & 31) >> 3);
   const int a_k = modp32(U * sx + kq - half, UW);
+  // this thread's four E_c roots of a chunk, loaded one chunk ahead (the
+  // table is read through L1, which two CTAs' shared memory leaves small)
+  auto roots_of = [&](int c, float2* w) {
+    if (tid < 4 * kTcN && kq < K && c < nch) {
+      const int v0 = c * kTcKc + vq;  // 4 | W / 2: the four columns share a sign
+      int n = modp32((v0 < W / 2 ? v0 : v0 - W) * a_k, UW);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        w[e] = __ldg(roots + n);
+        n += a_k;
+        if (n >= UW) n -= UW;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) w[e] = make_float2(0.f, 0.f);
+    }
+  };
+  float2 wn[4];
+  roots_of(0, wn);
   const uint32_t id128 = tc_idesc_tf32(kTcRows, 4 * kTcN, false);
   const uint32_t id64 = tc_idesc_tf32(kTcRows, 2 * kTcN, false);
   // descriptors of buffer 0; the other planes differ only in the start field
@@ -513,8 +526,13 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
   };
   for (int c = 0; c < nch; ++c) {
     const int b = c & 1;
-    cp_async_wait<1>();
-    __syncthreads();  // chunk c has landed
+    float4 xc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      xc[i] = xn[i];
+      xn[i] = xn2[i];
+    }
+    fetch(xn2, c + 2);  // in flight while this chunk and the next are split
     bool ok = true;
     if (c >= 2) {  // the MMAs of chunk c - 2 still read plane buffer b
       ok = mbar_wait_bounded(&mbar[b], (ph >> b) & 1u, kLimit);
@@ -527,13 +545,12 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
     char* Ap = pl + b * kTcBuf;
     char* Bp = Ap + 4 * kTcAPlane;
     {  // X split: thread -> row m, core-matrix columns q = 2 (tid / 128) + 0..1
-      const int m = tid & (kTcRows - 1);
-      const float2* src = raw + b * kTcRows * kTcRawPitch + m * kTcRawPitch;
+      const int m = xm;
 #pragma unroll
       for (int qq = 0; qq < 2; ++qq) {
         const int q = 2 * (tid >> 7) + qq;
-        const float4 x0 = *reinterpret_cast<const float4*>(src + 4 * q);
-        const float4 x1 = *reinterpret_cast<const float4*>(src + 4 * q + 2);
+        const float4 x0 = xc[2 * qq];
+        const float4 x1 = xc[2 * qq + 1];
         const float re[4] = {x0.x, x0.z, x1.x, x1.z}, im[4] = {x0.y, x0.w, x1.y, x1.w};
         float4 rh, rl, ih, il;
         split4(re, rh, rl);
@@ -546,18 +563,11 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
       }
     }
     if (tid < 4 * kTcN) {  // E_c split: B1 = [Ecr | Eci], B2 = [-Eci | Ecr], lo parts 64 rows down
-      float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f}, nci[4];
-      if (kq < K) {
-        const int v0 = c * kTcKc + vq;  // 4 | W / 2: the four columns share a sign
-        int n = modp32((v0 < W / 2 ? v0 : v0 - W) * a_k, UW);
+      float cr[4], ci[4], nci[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 w = roots[n];
-          cr[e] = w.x;
-          ci[e] = w.y;
-          n += a_k;
-          if (n >= UW) n -= UW;
-        }
+      for (int e = 0; e < 4; ++e) {
+        cr[e] = wn[e].x;  // zero past K
+        ci[e] = wn[e].y;
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) nci[e] = -ci[e];
@@ -578,6 +588,7 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
       *reinterpret_cast<float4*>(B2 + l1) = nl;
       *reinterpret_cast<float4*>(B2 + l2) = rl;
     }
+    roots_of(c + 1, wn);  // in flight while this chunk's MMAs are issued and run
     fence_proxy_async();  // the planes, written through the generic proxy, go to the MMA
     __syncthreads();
     if (tid == 0) {
@@ -598,7 +609,6 @@ k_updft_tc(const float2* __restrict__ scratch, int npl, int M, int nparts,
       }
       tc_commit(&mbar[b]);
     }
-    stage(c + 2);  // this chunk's staging buffer has been split
   }
   {  // the last chunk's commit covers every MMA issued before it
     const int b = (nch - 1) & 1;
@@ -757,8 +767,7 @@ RefGeo make_refgeo(int W, int U, bool tc) {
   g.W = W;
   g.U = std::max(1, U);
   g.K = (int)std::ceil(1.5 * g.U);
-  g.tc = tc && g.U > 1 && g.K <= kTcN &&
-         (size_t)kTcFixed + (size_t)g.U * W * sizeof(float2) <= (size_t)smem_optin() - 1024;
+  g.tc = tc && g.U > 1 && g.K <= kTcN && (size_t)kTcFixed <= (size_t)smem_optin() - 1024;
   switch (W) {
     case 32: refgeo_fill<32>(g); break;
     case 64: refgeo_fill<64>(g); break;
@@ -853,7 +862,7 @@ cudaError_t launch_updft(const RefGeo& g, float2* scratch, int npl, int M, const
   const int nblocks = g.tc ? (g.W + kTcRows - 1) / kTcRows : g.W / g.RB;
   cudaError_t e = cudaSuccess;
   if (g.tc) {  // the shares are added by the last CTA of each patch
-    const size_t sm = (size_t)kTcFixed + (size_t)g.U * g.W * sizeof(float2);
+    const size_t sm = (size_t)kTcFixed;
     PTY_DISPATCH_W(g.W, e = launch_pdl(k_updft_tc<WW>, dim3(nblocks, npatch), dim3(256), sm, s,
                                        scratch, npl, M, nparts, cval, cidx, roots, g.U, g.K,
                                        part, ids, done, shift, gap, err));
