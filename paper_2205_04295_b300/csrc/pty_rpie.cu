@@ -645,7 +645,7 @@ cudaError_t launch_probe_apply(const Tiling& t, float2* P, const float2* pnum,
                                const float* pden, const float* osum, int nslots,
                                float alpha_P, float reg_eps, float* pmax_part,
                                cudaStream_t s) {
-  if (t.M <= 8)
+  if (t.M >= 2 && t.M <= 8)  // one mode: the per-pixel kernel has twice the threads a block
     return launch_pdl(k_probe_apply_pm, dim3(t.n_pmax), dim3(kPaX, t.M), 0, s, P, t.M,
                       t.W * t.W, pnum, pden, osum, nslots, alpha_P, reg_eps, pmax_part);
   return launch_pdl(k_probe_apply, dim3(t.n_pmax), dim3(256), 0, s, P, t.M, t.W * t.W, pnum,
