@@ -140,3 +140,29 @@ def test_gradient_under_non_default_tilings():
         assert abs(got[0][0] - ref[0][0]) <= 1e-5 * abs(ref[0][0])
         for a, b in zip(got[1:], ref[1:]):
             assert rel_l2(a, b) <= 1e-5
+
+
+def test_chunks_that_split_groups():
+    """The per-patch passes take chunks of the group-ordered positions that
+    need not end where a group ends (here 3 patches a chunk); the scatter
+    into dL/dO then runs per group part.  dL/dO and dL/dpos are the same
+    bits as with one chunk for all positions (each object pixel still takes
+    its contributions group by group, in the same order); dL/dP differs only
+    in how the probe partial sums are grouped."""
+    wl = synth.tiny(W=64, M=2, ny=5, nx=5, step=10.0, seed=46, photons=1e6)
+    wl.Hy += 2
+    wl.Hx += 2
+    d = build(wl)
+    O, P, pos = state(wl, d)
+    prob, t, ref = gpu_grad(wl, d, O, P, pos)
+    assert len(prob.groups()) > 1
+    tl = prob.tiling()
+    prob.set_tiling(tl["R"], tl["ppc"], tl["CB"], 3 * (wl.M + 1) * wl.W * wl.W * 8, tl["ppcb"])
+    L, gO, gP, gpos = [to_host(x) for x in prob.loss_grad(*t)]
+    assert abs(L[0] - ref[0][0]) <= 1e-6 * abs(ref[0][0])
+    np.testing.assert_array_equal(gO, ref[1])
+    np.testing.assert_array_equal(gpos, ref[3])
+    assert rel_l2(gP, ref[2]) <= 1e-6
+    Lo, gOo, gPo, gposo = grad.loss_and_grad(O, P, pos.astype(np.float64), d["I"], delta=1.0)
+    assert rel_l2(gO, gOo) <= 1e-5
+    assert rel_l2(gP, gPo) <= 1e-5
