@@ -560,24 +560,26 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0, in
   // the batch slot of the group's first patch (its planes in the scratch)
   const int p0 = boff > 0 ? boff : 0;
   float2* scr = h->scratch + (size_t)p0 * tl.npl * h->W * h->W;
+  // passes A and B take patches per CTA re-chosen for the chunk's size
   for (int c0 = 0; c0 < n; c0 += Qc) {
     const int nc = std::min(Qc, n - c0);
     const int* idc = ids + c0;
+    const pty::Tiling tc = pty::tiling_for_chunk(tl, nc);
     {
       pty_handle::Mark m(h, PTY_K_ROWS_FWD);
-      CU(pty::launch_rows_fwd(tl, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, scr,
+      CU(pty::launch_rows_fwd(tc, h->O, h->Hx, h->P, idc, h->corners, nc, h->tw, scr,
                               h->omax_part, h->stream));
     }
     {
       pty_handle::Mark m(h, PTY_K_COLS);
-      CU(pty::launch_cols(tl, scr, h->I, idc, nc, h->tw, h->inv_w, p->eps,
+      CU(pty::launch_cols(tc, scr, h->I, idc, nc, h->tw, h->inv_w, p->eps,
                           h->err_part,
                           refine ? (h->tma_br ? &h->tmap_br : nullptr) : (h->tma_b ? &h->tmap_b : nullptr),
                           h->tma_err, h->stream, refine == 2 ? h->M : -1, p0 * tl.npl));
     }
     {
       pty_handle::Mark m(h, PTY_K_ROWS_INV);
-      CU(pty::launch_rows_inv(tl, h->O, h->Hx, h->P, idc, h->corners, nc, scr,
+      CU(pty::launch_rows_inv(tc, h->O, h->Hx, h->P, idc, h->corners, nc, scr,
                               h->omax_part, h->pmax_part, h->tw, a, h->pnum, h->pden, h->osum,
                               c0 > 0, h->tma_err, h->stream, refine == 1 ? 1 : 0));
     }
@@ -600,7 +602,7 @@ int run_group(pty_handle* h, int g, const pty_rpie_params* p, int refine = 0, in
     }
   }
   if (p->update_probe) {
-    const int used = (std::min(Qc, n) + tl.ppc - 1) / tl.ppc;
+    const int used = (std::min(Qc, n) + tl.ppcc - 1) / tl.ppcc;
     pty_handle::Mark m(h, PTY_K_PROBE);
     CU(pty::launch_probe_apply(tl, h->P, h->pnum, h->pden, h->osum, used, p->alpha_P,
                                p->reg_eps, h->pmax_part, h->stream));
@@ -833,6 +835,8 @@ int pty_init_problem(const pty_problem_desc* d, pty_handle** out) {
   h->tlr = pty::make_tiling(h->W, h->M, true);
   if (cudaError_t e = pty::set_smem_limits(h->tl); e != cudaSuccess)
     return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
+  pty::fill_residency(h->tl);
+  pty::fill_residency(h->tlr);
   if (cudaError_t e = pty::set_grad_smem(h->tl); e != cudaSuccess)
     return bail(fail(PTY_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)));
   if (!pty::tiling_fits(h->tl) || !pty::tiling_fits(h->tlr))
@@ -1520,6 +1524,8 @@ int pty_set_tiling(pty_handle* h, const pty_tiling* t) {
   CU(pty::set_smem_limits(h->tl));
   CU(pty::set_smem_limits(h->tlr));
   CU(pty::set_grad_smem(h->tl));
+  pty::fill_residency(h->tl);
+  pty::fill_residency(h->tlr);
   return PTY_OK;
 }
 

@@ -24,6 +24,8 @@ struct Tiling {
   int ppc;       // patches per CTA, row passes
   int CB;        // columns per CTA, column pass
   int ppcb;      // patches per CTA, column pass
+  int ppcc;      // patches per CTA, pass C (ppc unless re-chosen for a chunk)
+  int resA, resB, resC;  // CTAs of the three pass kernels resident on the device (0: unknown)
   int thrA, thrB, thrC;
   size_t smA, smB, smC, smI;  // dynamic shared memory (bytes)
   size_t smA_staged;          // pass A with its probe rows in shared memory (batched form)
@@ -54,6 +56,15 @@ Tiling make_tiling(int W, int M, bool refine = false, int max_threads_b = 512, i
                    int ppc_req = 0, int CB_req = 0);
 int lanes_per_line(int W);
 cudaError_t set_smem_limits(const Tiling& t);
+// Fill t.resA / resB / resC (after set_smem_limits).
+void fill_residency(Tiling& t);
+// The tiling for a chunk of n patches: the patches per CTA of pass A (ppc)
+// and of the column pass (ppcb) re-chosen near the tuned values so that each
+// kernel's CTAs end close to a whole number of waves (pass A's dynamic shared
+// memory follows ppc).  Neither changes a result (no sum runs across a CTA's
+// patches there); pass C keeps ppcc, whose probe-sum slots the results do
+// depend on.
+Tiling tiling_for_chunk(const Tiling& t, int n);
 
 // Twiddle table of the line FFTs: slot e holds w_W^m = exp(-2 pi i m / W) with
 // m = tw_exponent(W, e) (host, double -> float).

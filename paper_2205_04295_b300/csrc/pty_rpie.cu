@@ -7,6 +7,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdint>
 
@@ -488,6 +489,7 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   if (R_req > 0) R = R_req;
   t.R = R;
   t.ppc = ppc_req > 0 ? ppc_req : 4;
+  t.ppcc = t.ppc;
   t.ppcb = 2;
   int CB = pow2_floor(std::max(1, max_threads_b / (M * L)));
   CB = std::max(2, std::min(16, CB));  // M * CB * L <= max_threads_b threads
@@ -517,6 +519,82 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   t.smC = t.pstage ? smC1 : smC0;
   t.n_pmax = std::max(1, std::min(1024, W * W / 256));
   return t;
+}
+
+void fill_residency(Tiling& t) {
+  int dev = 0, nsm = 0;
+  t.resA = t.resB = t.resC = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const void *fa = nullptr, *fb = nullptr, *fc = nullptr;
+  const bool big = t.thrB > kColsSmall;
+  auto pick = [&](auto wtag) {
+    constexpr int WW = decltype(wtag)::value;
+    fa = (const void*)k_rows_fwd<WW>;
+    fc = t.pstage ? (const void*)k_rows_inv<WW, true> : (const void*)k_rows_inv<WW, false>;
+    switch (t.CB) {
+      case 2: fb = big ? (const void*)k_cols<WW, 2, false, true> : (const void*)k_cols<WW, 2, false, false>; break;
+      case 4: fb = big ? (const void*)k_cols<WW, 4, false, true> : (const void*)k_cols<WW, 4, false, false>; break;
+      case 8: fb = big ? (const void*)k_cols<WW, 8, false, true> : (const void*)k_cols<WW, 8, false, false>; break;
+      default: fb = big ? (const void*)k_cols<WW, 16, false, true> : (const void*)k_cols<WW, 16, false, false>; break;
+    }
+  };
+  switch (t.W) {
+    case 32: pick(std::integral_constant<int, 32>{}); break;
+    case 64: pick(std::integral_constant<int, 64>{}); break;
+    case 96: pick(std::integral_constant<int, 96>{}); break;
+    case 128: pick(std::integral_constant<int, 128>{}); break;
+    case 192: pick(std::integral_constant<int, 192>{}); break;
+    default: pick(std::integral_constant<int, 256>{}); break;
+  }
+  int na = 0, nb = 0, nc = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, fa, t.thrA, t.smA) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fb, t.thrB, t.smB) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nc, fc, t.thrC, t.smC) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  t.resA = na * nsm;
+  t.resB = nb * nsm;
+  t.resC = nc * nsm;
+}
+
+namespace {
+// Patches per CTA for a kernel whose chunk of n patches makes bx CTAs per
+// patch group of q: the q in [lo, hi] that minimises whole waves x (q + a
+// CTA's fixed cost of about 3/4 of a patch), the tuned q0 on ties.
+int pick_per_cta(int n, int bx, int res, int q0, int lo, int hi) {
+  if (res <= 0 || n <= 0) return q0;
+  auto cost = [&](int q) {
+    const long long ctas = (long long)((n + q - 1) / q) * bx;
+    return (double)((ctas + res - 1) / res) * (q + 0.75);
+  };
+  int best = q0;
+  double bc = cost(q0);
+  for (int q = lo; q <= hi; ++q) {
+    const double c = cost(q);
+    if (c < bc - 1e-9 || (c < bc + 1e-9 && std::abs(q - q0) < std::abs(best - q0))) {
+      best = q;
+      bc = c;
+    }
+  }
+  return best;
+}
+}  // namespace
+
+Tiling tiling_for_chunk(const Tiling& t, int n) {
+  Tiling c = t;
+  const int qa = pick_per_cta(n, t.W / t.R, t.resA, t.ppc, std::max(1, t.ppc / 2),
+                              std::min(64, 2 * t.ppc));
+  c.ppcb = pick_per_cta(n, t.W / t.CB, t.resB, t.ppcb, 1, std::min(64, 2 * t.ppcb + 1));
+  // pass A's corner list is ppc long
+  c.smA = t.smA + ((size_t)qa - t.ppc) * sizeof(float2);
+  c.smA_staged = t.smA_staged + ((size_t)qa - t.ppc) * sizeof(float2);
+  c.ppc = qa;
+  return c;
 }
 
 cudaError_t set_smem_limits(const Tiling& t) {
@@ -628,15 +706,15 @@ cudaError_t launch_rows_inv(const Tiling& t, float2* O, int Hx, const float2* P,
                             float* osum, int accumulate, int* err, cudaStream_t s,
                             int refine) {
   if (npatch <= 0) return cudaSuccess;
-  dim3 grid(t.W / t.R, (npatch + t.ppc - 1) / t.ppc);
+  dim3 grid(t.W / t.R, (npatch + t.ppcc - 1) / t.ppcc);
   cudaError_t e = cudaSuccess;
   const int rf = refine < 0 ? t.refine : (refine && t.refine);
   PTY_DISPATCH_W(t.W, e = t.pstage
-      ? launch_pdl(k_rows_inv<WW, true>, grid, dim3(t.thrC), t.smC, s, O, Hx, P, t.M, t.R, t.ppc,
+      ? launch_pdl(k_rows_inv<WW, true>, grid, dim3(t.thrC), t.smC, s, O, Hx, P, t.M, t.R, t.ppcc,
                    ids, corners, npatch, scratch, omax_part, pmax_part, t.n_pmax, tw, a, pnum,
                    pden, osum, accumulate, t.npl, rf, err)
       : launch_pdl(k_rows_inv<WW, false>, grid, dim3(t.thrC), t.smC, s, O, Hx, P, t.M, t.R,
-                   t.ppc, ids, corners, npatch, scratch, omax_part, pmax_part, t.n_pmax, tw, a,
+                   t.ppcc, ids, corners, npatch, scratch, omax_part, pmax_part, t.n_pmax, tw, a,
                    pnum, pden, osum, accumulate, t.npl, rf, err));
   return e;
 }
