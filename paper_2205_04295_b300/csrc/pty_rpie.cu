@@ -40,8 +40,15 @@ k_cols(float2* __restrict__ scratch, int M,
        const float2* __restrict__ tw_g, float inv_w, float eps,
        float* __restrict__ err_part, int npl, int ppcb, int npatch,
        const __grid_constant__ CUtensorMap tmap, int use_tma, int* err, int xb, int plane0) {
+  // Patch blocks in reverse order: CTAs are dispatched in blockIdx order, so
+  // this pass starts on the patches pass A wrote last and pass C (forward)
+  // starts on the ones this pass writes last.  A group's far field is larger
+  // than L2 at big W and M; in one direction every pass would miss on all of
+  // it (least-recently-used eviction of a stream larger than the cache).
+  // Each patch's outputs are the same in any order.
   cols_body<W, CB, GRAD>(scratch, M, I, ids, tw_g, inv_w, eps, err_part, npl, ppcb, npatch,
-                         blockIdx.x, blockIdx.y, use_tma ? &tmap : nullptr, err, xb, plane0);
+                         blockIdx.x, gridDim.y - 1 - blockIdx.y, use_tma ? &tmap : nullptr, err,
+                         xb, plane0);
 }
 
 template <int W, bool PSTAGE>
