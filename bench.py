@@ -65,11 +65,12 @@ def per_pass_flops(W, M):
 
 # DRAM bytes per pattern update of each pass, warm L2: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum with --cache-control none on
-# `bench.py --workload spiral_256_n2000` (256^2 x 5 modes; launches 41-80 of
-# the three passes and the probe update, groups 10-19, 133 patches).  Valid
-# for the pass kernels as profiled; a launch's traffic is this times its
-# patches.
-DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 0.252e6, "cols": 0.390e6, "rows_inv": 0.104e6}}
+# `bench.py` (the headline spiral, 10^4 positions; launches 81-120 of the
+# three passes and the probe update: groups 20-29, 674 patches).  A group's
+# far field (about 67 patches x 2.62 MB) is larger than L2, so most of it
+# goes to HBM and back between the passes.  Valid for the pass kernels as
+# profiled; a launch's traffic is this times its patches.
+DRAM_PER_PATCH = {(256, 5): {"rows_fwd": 2.648e6, "cols": 4.018e6, "rows_inv": 3.741e6}}
 
 
 def fp32_peak_tflops():
@@ -467,6 +468,10 @@ def run_ours(args, wl, rank, world, local):
            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                         "traffic_unit": "DRAM bytes per launch (warm L2, scaled from ncu)",
+                        # the same launch's HBM rate at that traffic, against the
+                        # measured copy bandwidth
+                        "traffic_gbs": traffic / (avg_ms / 1e3) / 1e9 if traffic else None,
+                        "traffic_frac_of_hbm": traffic / (avg_ms / 1e3) / 1e9 / hbm if traffic else None,
                         "peak_source": "148 SM x 128 FP32 lanes x 2 x 2032 MHz",
                         "peak_measured": ffma, "frac_of_measured": achieved / ffma if ffma else None,
                         "peak_measured_source": "FMA-chain kernel (pty_measure_fp32_peak)",
