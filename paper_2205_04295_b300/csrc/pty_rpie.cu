@@ -524,7 +524,11 @@ Tiling make_tiling(int W, int M, bool refine, int max_threads_b_req, int R_req, 
   const size_t smC1 = smC0 + (size_t)M * R * W * sizeof(float2);
   t.pstage = pstage_pays(W, t.thrC, smC0, smC1) ? 1 : 0;
   t.smC = t.pstage ? smC1 : smC0;
-  t.n_pmax = std::max(1, std::min(1024, W * W / 256));
+  // probe-update blocks (and probe-intensity maxima): one per 256 pixels, or
+  // one per 128 where that would leave SMs idle (W <= 192; at 128^2 / 3
+  // modes, 137 groups: 4.34 -> 4.00 ms per iteration)
+  t.n_pmax = W * W / 256 < 148 ? W * W / 128 : W * W / 256;
+  t.n_pmax = std::max(1, std::min(1024, t.n_pmax));
   return t;
 }
 
