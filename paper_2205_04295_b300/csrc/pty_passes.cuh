@@ -440,15 +440,15 @@ PTY_D void cols_body(float2* __restrict__ scratch, int M,
 
 
 // ---------------------------------------------------------------- pass C
-// Request (cp.async) patch slot lp's far-field rows [r0, r0 + R) of the M
-// modes into `zst` ([mode][row][column]) and its crop rows into `ost`.
+// Request patch slot lp's far-field rows [r0, r0 + R) of the M modes into
+// `zst` ([mode][row][column]) (rows_inv_stage_far), and with rows_inv_stage
+// also its crop rows into `ost`.  With `mbar`, thread 0 moves the far-field
+// rows by bulk copies (one per row, completing on the mbarrier); otherwise
+// every thread issues 16-byte cp.async copies.  The crop rows (any
+// alignment) always take cp.async.
 template <int W>
-// With `mbar`, thread 0 moves the far-field rows by bulk copies (one per
-// row, completing on the mbarrier); otherwise every thread issues 16-byte
-// cp.async copies.  The crop rows (any alignment) always take cp.async.
-PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 cc, int lp,
-                          int npl, int M, int R, int r0, float2* zst, float2* ost,
-                          unsigned long long* mbar) {
+PTY_D void rows_inv_stage_far(const float2* scratch, int lp, int npl, int M, int R, int r0,
+                              float2* zst, unsigned long long* mbar) {
   if (mbar) {
     if (threadIdx.x == 0) {
       fence_proxy_async();  // the stage was just read through the generic proxy
@@ -468,6 +468,12 @@ PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 c
                    scratch + (((size_t)lp * npl + k) * W + r0 + r) * W + 2 * h);
     }
   }
+}
+template <int W>
+PTY_D void rows_inv_stage(const float2* scratch, const float2* O, int Hx, int2 cc, int lp,
+                          int npl, int M, int R, int r0, float2* zst, float2* ost,
+                          unsigned long long* mbar) {
+  rows_inv_stage_far<W>(scratch, lp, npl, M, R, r0, zst, mbar);
   stage_crop_rows<W>(O, Hx, cc, R, r0, ost);
 }
 
@@ -574,6 +580,10 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   for (int e = threadIdx.x; e < W; e += blockDim.x) tw[e] = tw_g[e];
   if (mbar && threadIdx.x == 0) mbar_init(mbar, 1 + stalled_arrivals(err));
   pdl_wait();  // everything below is written by earlier kernels
+  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
+  // the first patch's far-field rows need no corner: they are requested
+  // before the prologue's loads, its crop rows once the corners are in
+  if (p0 < p1) rows_inv_stage_far<W>(scratch, p0, npl, M, R, r0, zst, mbar);
   if (threadIdx.x < 32) {
     float m = 0.f;
     for (int i = threadIdx.x; i < n_pmax; i += 32) m = fmaxf(m, pmax_part[i]);
@@ -610,7 +620,6 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
     nm[n1] = make_float2(0.f, 0.f);
     if constexpr (PK_REG) pk[n1] = own ? prow[G::N2 * n1 + lane] : make_float2(0.f, 0.f);
   }
-  const int p0 = by * ppc, p1 = min(npatch, p0 + ppc);
   // the CTA's corners and crop maxima max_r |o_j|^2 (reduced over the row
   // blocks of pass A), once: no dependent global loads inside the patch loop
   {
@@ -625,8 +634,7 @@ PTY_D void rows_inv_body(float2* O, int Hx, const float2* P, int M,
   }
   __syncthreads();
   float osum_local = 0.f;
-  if (p0 < p1)
-    rows_inv_stage<W>(scratch, O, Hx, scor[0], p0, npl, M, R, r0, zst, ostash, mbar);
+  if (p0 < p1) stage_crop_rows<W>(O, Hx, scor[0], R, r0, ostash);
   cp_async_commit();
   for (int lp = p0; lp < p1; ++lp) {
     const int2 cc = scor[lp - p0];
