@@ -30,6 +30,8 @@ def workloads():
     return {
         "spiral_256": lambda: synth.spiral_256(),
         "spiral_256_n2000": lambda: synth.spiral_256(n=2000),
+        # 2000 positions over the headline's extent: groups of its size
+        "spiral_256_n2000_spread5": lambda: synth.spiral_256(n=2000, spread=5.0),
         "plain_64": lambda: synth.plain_rpie_64(),
         "refine_128": lambda: synth.refine_128(),
         "sweep_256": lambda: synth.sweep_256(),

@@ -225,14 +225,18 @@ def refine_128(seed=2000):
                     lr=0.5, seed=seed)
 
 
-def spiral_256(seed=3000, n=10000):
+def spiral_256(seed=3000, n=10000, spread=1.0):
     """256x256 patterns, 5 modes, Fermat spiral of 10^4 positions
-    (r = 12.5 sqrt(k), 137.508 deg), object 2800x2800, 1e6 photons."""
+    (r = 12.5 sqrt(k), 137.508 deg), object 2800x2800, 1e6 photons.
+    spread > 1 scales the radii by sqrt(spread): n positions over the extent
+    n * spread would cover (a sparser scan whose disjoint groups have the
+    size of the denser scan's with n * spread positions)."""
     W, H = 256, 2800
-    sp = fermat_spiral(n, 12.5)
+    sp = fermat_spiral(n, 12.5 * math.sqrt(spread))
     c = (H - W) / 2.0
     true = sp + c
-    return Workload("spiral_w256_m5_n%d" % n, W, 5, H, H, 1e6, _occ(5), true,
+    name = "spiral_w256_m5_n%d" % n + ("" if spread == 1.0 else "_spread%g" % spread)
+    return Workload(name, W, 5, H, H, 1e6, _occ(5), true,
                     true.astype(np.float32), n_iter=1, seed=seed)
 
 
