@@ -25,3 +25,25 @@ def test_batch_shard_partitions_and_balances():
         assert flat == list(range(64))
         loads = [sum(costs[p] for p in s) for s in shards]
         assert max(loads) <= 1.1 * sum(costs) / world + max(costs)
+
+
+def test_spread_spiral_has_the_headline_group_size():
+    """The profiling workload `spiral_256_n2000_spread5` stands in for the
+    headline scan at a fifth of its positions: same extent, so its greedy
+    disjoint groups (whose far field sets the passes' L2 behaviour) have the
+    headline's size.  spread = 1 is the headline scan itself."""
+    import numpy as np
+    import bench
+    from paper_2205_04295_b300 import pty
+    wls = bench.workloads()
+    head = wls["spiral_256"]()
+    assert np.array_equal(synth.spiral_256(spread=1.0).pos_true, head.pos_true)
+    sparse = wls["spiral_256_n2000_spread5"]()
+    assert sparse.N == 2000 and sparse.W == head.W and sparse.M == head.M
+    sizes = {}
+    for name, wl in (("head", head), ("sparse", sparse)):
+        g = pty.group_positions(wl.pos.astype(np.float32), wl.W)
+        sizes[name] = np.array([len(x) for x in g])
+    # 164 groups of 61 patches on average against 39 of 51
+    assert abs(np.median(sizes["sparse"]) / np.median(sizes["head"]) - 1.0) < 0.2
+    assert sizes["sparse"].max() >= 0.9 * sizes["head"].max()
