@@ -30,7 +30,7 @@ def workloads():
     return {
         "spiral_256": lambda: synth.spiral_256(),
         "spiral_256_n2000": lambda: synth.spiral_256(n=2000),
-        # 2000 positions over the headline's extent: groups of its size
+        # 2000 positions over the 10^4-position spiral's extent: groups of its size
         "spiral_256_n2000_spread5": lambda: synth.spiral_256(n=2000, spread=5.0),
         "plain_64": lambda: synth.plain_rpie_64(),
         "refine_128": lambda: synth.refine_128(),
@@ -67,7 +67,7 @@ def per_pass_flops(W, M):
 
 # DRAM bytes per pattern update of each pass, warm L2: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum with --cache-control none on
-# `bench.py` (the headline spiral, 10^4 positions; launches 81-120 of the
+# `bench.py` (the 256^2 / 5-mode spiral of 10^4 positions; launches 81-120 of the
 # three passes and the probe update: groups 20-29, 674 patches).  A group's
 # far field (about 67 patches x 2.62 MB) is larger than L2, so most of it
 # goes to HBM and back between the passes.  Valid for the pass kernels as

@@ -27,11 +27,11 @@ def test_batch_shard_partitions_and_balances():
         assert max(loads) <= 1.1 * sum(costs) / world + max(costs)
 
 
-def test_spread_spiral_has_the_headline_group_size():
+def test_spread_spiral_has_the_group_size_of_the_full_spiral():
     """The profiling workload `spiral_256_n2000_spread5` stands in for the
-    headline scan at a fifth of its positions: same extent, so its greedy
-    disjoint groups (whose far field sets the passes' L2 behaviour) have the
-    headline's size.  spread = 1 is the headline scan itself."""
+    10^4-position spiral at a fifth of its positions: same extent, so its
+    greedy disjoint groups (whose far field sets the passes' L2 behaviour)
+    have the full spiral's size.  spread = 1 is the full spiral itself."""
     import numpy as np
     import bench
     from paper_2205_04295_b300 import pty
